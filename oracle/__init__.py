@@ -1,0 +1,23 @@
+"""CPU FP64 oracle for the structure-preserving Bethe--Salpeter solver.
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product path may import, call or
+execute this package: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use it.
+
+It shares no code with the CUDA path. Two routes are provided:
+
+* :mod:`oracle.definition` -- the result Algorithm 1 must reach, written from
+  the definitions (Eq. 1, Eq. GMG, Theorem 3, Eq. absp) through the
+  Hermitian-definite pencil  S x = (1/lambda) Omega x.
+* :mod:`oracle.alg1` -- Algorithm 1 and Algorithm 3 restated step by step in
+  the paper's order and notation (M, L, W, T, D, Phi, Y_+), used to check the
+  intermediate results of the device pipeline stage by stage.
+
+:mod:`oracle.brute` adds a 50-digit mpmath eigen-decomposition of H for
+n <= 4, one of the pins that ties the oracle to something other than itself.
+
+Parity status: every function here is pinned by tests in
+``tests/test_oracle_pins.py`` except the eigenvector phase and the basis inside
+a degenerate cluster, which are not unique (parity unpinned by nature; tests
+compare phase-free quantities there).
+"""

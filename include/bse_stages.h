@@ -1,0 +1,94 @@
+/*
+ * bse_stages.h -- stage-level C ABI of the BSE solver: one entry point per
+ * step of Algorithm 1 / Algorithm 3, on DEVICE pointers, asynchronous on the
+ * given stream (a cudaStream_t passed as void*; NULL = legacy default stream).
+ * These are what bse_solve chains; they are exported for testing each stage
+ * against the oracle and for timing each kernel on its own.
+ *
+ * Shared rules
+ *   - All matrices are column-major with the given leading dimension, except
+ *     the eigenvector matrix Vs of bse_stage_tdeig (row-major, see there).
+ *   - `fp32 = 1` selects FP32 storage and arithmetic for a stage that has both
+ *     (the mixed path); otherwise FP64.
+ *   - `work` is caller-owned device scratch of at least the *_worksize bytes,
+ *     256-byte aligned; its contents on entry do not matter.
+ *   - `dev_status` points to 16 zero-initialised device bytes (4 ints); a stage
+ *     that detects a failure stores {code, info} there (first failure wins) and
+ *     never traps. The host reads it after the stream is synchronised.
+ *   - Return value: BSE_OK, BSE_ERR_ARG on a bad argument (checked on the host
+ *     before any launch), BSE_ERR_CUDA on a launch error.
+ */
+#ifndef BSE_GB300_STAGES_H
+#define BSE_GB300_STAGES_H
+
+#include <stddef.h>
+
+#include "bse.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Algorithm 1 step 1 (Theorem 2, Eq. embedding):
+ *   M = [Re(A+B) Im(A-B); -Im(A+B) Re(A-B)]   (2n x 2n real symmetric, FULL storage)
+ * A, B: n x n complex128 (interleaved), ld in complex elements, lower triangles read.
+ * M: FP64, ldm >= 2n. Mf (nullable): an FP32 copy, ldmf >= 2n. */
+int bse_stage_form_M(int n, const double* A, int lda, const double* B, int ldb, double* M, int ldm, float* Mf,
+                     int ldmf, void* stream);
+
+/* Algorithm 1 step 2: M = L L^T in place (lower triangle; the strict upper
+ * triangle is not touched). A non-positive pivot (Eq. cond violated) stores
+ * {BSE_ERR_NOT_DEFINITE, 1-based column} in dev_status. A: m x m, FP64 or FP32. */
+size_t bse_stage_potrf_worksize(int m, int fp32);
+int bse_stage_potrf(int m, void* A, int lda, int fp32, void* work, int* dev_status, void* stream);
+
+/* Algorithm 1 step 3: W = L^T J L with J = [0 I; -I 0] (Eq. J). L: 2n x 2n lower
+ * (the upper triangle is ignored). Writes the STRICT LOWER triangle of W and its
+ * diagonal (zero); W's upper-right n x n block is used as scratch. */
+int bse_stage_form_W(int n, const void* L, int ldl, void* W, int ldw, int fp32, void* stream);
+
+/* Algorithm 3 step 1 (remark 1): W = U T U^T by blocked skew-symmetric Householder
+ * reduction, m = 2n. Reads W's strict lower triangle; on return e[k] = T[k+1,k]
+ * (k = 0..m-2, FP64), tau[k] (FP64 or FP32 like W) and W[k+1:m, k] = v_k with
+ * v_k[0] = 1 (H_k = I - tau_k v_k v_k^T, U = H_0 H_1 ... H_{m-2}). */
+size_t bse_stage_tridiag_worksize(int m, int fp32);
+int bse_stage_tridiag(int m, void* W, int ldw, double* e, void* tau, int fp32, void* work, void* stream);
+
+/* Algorithm 3 step 2 (remark 2): positive eigenpairs of Tsym = -i D^H T D (zero
+ * diagonal, off-diagonal -e[k]), D = diag(i^k), k = 0..m-1, m even. FP64.
+ *   lam: n = m/2 eigenvalues, ascending.
+ *   Vs (nullable): ROW-major m x n (element (k, j) at k*n + j): the eigenvectors
+ *   with the D phase folded in, Vs[k][j] = s_k v_j[k], s_k = +1,+1,-1,-1 for
+ *   k mod 4 = 0,1,2,3 (so D v_j = even rows + i * odd rows of Vs). */
+size_t bse_stage_tdeig_worksize(int m);
+int bse_stage_tdeig(int m, const double* e, double* lam, double* Vs, void* work, int* dev_status, void* stream);
+
+/* Algorithm 3 steps 3-6 with the Lambda^{-1/2} of Algorithm 1 step 5:
+ * Phi = L U (L overwritten by Phi), Y+ = Q Phi D V+, X = diag(I,-I) Y+ Lambda^{-1/2},
+ * Y = diag(I,-I) X. L, W, tau: FP64 or FP32 (fp32); Vs, lam: FP64 as produced by
+ * bse_stage_tdeig; X, Y (Y nullable): 2n x n complex128, ldx >= 2n. */
+size_t bse_stage_backtransform_worksize(int m, int fp32);
+int bse_stage_backtransform(int m, void* L, int ldl, const void* W, int ldw, const void* tau, const double* Vs,
+                            const double* lam, double* X, double* Y, int ldx, int fp32, void* work, void* stream);
+
+/* Eq. absp weights w_j = (d_r^H x_j)(y_j^H d_l)/(y_j^H x_j), y_j = diag(I,-I) x_j.
+ * X: 2n x n complex128 (ldx >= 2n); d_r, d_l: 2n complex128; w: n complex128. */
+int bse_stage_weights(int n, const double* X, int ldx, const double* d_r, const double* d_l, double* w,
+                      void* stream);
+
+/* FP64 structure-preserving refinement of (lam, X) in place (X: 2n x n complex128,
+ * ld 2n) against the FP64 M of bse_stage_form_M, at most max_sweeps sweeps of a
+ * Newton-type correction on the pencil M u = lambda (-iJ) u, u = Q^H x (Theorem 2,
+ * Eq. GMG, Theorem 3). The negative half stays the exact conjugate, so the +/-
+ * pairing and y = diag(I,-I) x are preserved. SYNCHRONISES the stream (it reads
+ * the convergence measures on the host between sweeps).
+ * diag3 (nullable, host): {max scaled residual, max rel. eigenvalue change of the
+ * last sweep, max rel. change of the first sweep}. */
+size_t bse_stage_refine_worksize(int n);
+int bse_stage_refine(int n, const double* M, double* lam, double* X, int max_sweeps, void* work, int* dev_status,
+                     void* stream, int* sweeps, double* diag3);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSE_GB300_STAGES_H */

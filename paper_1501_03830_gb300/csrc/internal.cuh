@@ -1,0 +1,41 @@
+// Internal (C++) entry points of the pipeline stages, shared by the solver,
+// the batched solver and the request loop.
+#pragma once
+
+#include "common.cuh"
+
+namespace bse {
+
+int form_M(int n, const double* A, int lda, const double* B, int ldb, double* M, int ldm, float* Mf, int ldmf,
+           cudaStream_t s);
+
+template <typename T>
+size_t potrf_worksize(int m);
+template <typename T>
+int potrf(int m, T* A, long lda, void* work, DevStatus* st, cudaStream_t s);
+
+template <typename T>
+int form_W(int n, const T* L, long ldl, T* W, long ldw, cudaStream_t s);
+
+template <typename T>
+size_t trd_worksize(int m);
+template <typename T>
+int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStream_t st);
+
+int tdeig(int m, const double* e, double* lam, double* Vs, double* work, DevStatus* st, cudaStream_t s);
+
+template <typename T>
+size_t bt_worksize(int m);
+template <typename T>
+int backtransform(int m, T* L, long ldl, const T* W, long ldw, const T* tau, const double* Vs, const double* lam,
+                  double* X, double* Y, long ldx, void* work, cudaStream_t s);
+
+int weights(int n, const double* X, long ldx, const double* dr, const double* dl, double* w, cudaStream_t s);
+
+size_t refine_worksize(int n);
+// FP64 structure-preserving refinement of (lam, X) in place (X: 2n x n complex128, ld 2n),
+// against the FP64 M (2n x 2n). Returns BSE_OK and fills the diagnostics.
+int refine(int n, const double* M, double* lam, double* X, int max_sweeps, double tol, void* work,
+           DevStatus* st, cudaStream_t s, int* sweeps_done, double* resid, double* dlam_last, double* dlam_first);
+
+}  // namespace bse

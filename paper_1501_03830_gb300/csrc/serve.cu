@@ -1,0 +1,224 @@
+// Request loop (bse_submit / bse_poll) and batched solves.
+//
+// The loop keeps `slots` worker threads, each bound to its own stream and
+// workspace cache on the context's GPU, so requests that arrive while others
+// are running are admitted as soon as a slot is free AND their workspace fits
+// the HBM budget next to the ones in flight; their kernels then overlap on the
+// device. Admission is first-fit in arrival order over the waiting queue, so
+// a large request waiting for memory does not block small ones behind it
+// (it is admitted first once it fits). Device-resident state (A, B, M, L, the
+// reflectors, X) stays in the slot's workspace for the whole request; only the
+// requested results are copied back.
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.cuh"
+#include "solver.h"
+
+namespace bse {
+
+struct Pending {
+  uint64_t ticket;
+  bse_request req;
+  double t_submit;
+  size_t bytes;
+};
+
+struct ServeState {
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Pending> queue;
+  std::unordered_map<uint64_t, bse_result> done;
+  std::unordered_map<uint64_t, bool> known;
+  std::vector<std::thread> workers;
+  std::vector<bse_ctx*> slot_ctx;
+  size_t budget = 0, in_use = 0;
+  size_t queue_cap = 4096;
+  uint64_t next_ticket = 1;
+  int running = 0;
+  bool stop = false;
+  std::chrono::steady_clock::time_point t0;
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+static size_t request_bytes(const bse_request& r) {
+  return workspace_bytes(r.n, r.precision) + 64 * (size_t)r.n;
+}
+
+static void worker_main(ServeState* S, bse_ctx* c) {
+  cudaSetDevice(c->device);
+  for (;;) {
+    Pending p;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      for (;;) {
+        if (S->stop && S->queue.empty()) return;
+        // first request (arrival order) whose workspace fits next to the running ones
+        auto it = S->queue.begin();
+        for (; it != S->queue.end(); ++it)
+          if (S->in_use + it->bytes <= S->budget || S->running == 0) break;
+        if (it != S->queue.end()) {
+          p = *it;
+          S->queue.erase(it);
+          S->in_use += p.bytes;
+          ++S->running;
+          break;
+        }
+        S->cv.wait_for(lk, std::chrono::milliseconds(50));
+      }
+    }
+    bse_result res{};
+    res.n = p.req.n;
+    res.t_submit = p.t_submit;
+    res.t_start = S->now();
+    bse_info info;
+    int rc = BSE_OK;
+    bse_sol* sol = nullptr;
+    const bool want_w = p.req.w && p.req.d_r && p.req.d_l;
+    rc = bse_solve(c, p.req.n, p.req.A, p.req.n, p.req.B, p.req.n, p.req.precision, p.req.lambda, p.req.X, nullptr,
+                   want_w ? &sol : nullptr, &info);
+    if (rc == BSE_OK && want_w) rc = bse_spectrum(c, sol, p.req.d_r, p.req.d_l, p.req.w);
+    if (sol) bse_sol_free(sol);
+    // keep the slot's cache to one workspace so the budget accounting holds
+    while (c->ws.size() > 1) {
+      auto victim = c->ws.begin();
+      for (auto i = c->ws.begin(); i != c->ws.end(); ++i)
+        if (i->second.last_use < victim->second.last_use) victim = i;
+      victim->second.release();
+      c->ws.erase(victim);
+    }
+    res.status = rc;
+    res.refine_dlam = info.refine_dlam;
+    res.t_done = S->now();
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->in_use -= p.bytes;
+      --S->running;
+      S->done[p.ticket] = res;
+    }
+    S->cv.notify_all();
+  }
+}
+
+}  // namespace bse
+
+using namespace bse;
+
+extern "C" int bse_serve_start(bse_ctx* c, int slots) {
+  if (!c || slots < 1 || slots > 64) return BSE_ERR_ARG;
+  if (c->serve) return BSE_OK;
+  ServeState* S = new ServeState();
+  S->t0 = std::chrono::steady_clock::now();
+  S->budget = c->budget;
+  for (int i = 0; i < slots; ++i) {
+    bse_ctx* sc = nullptr;
+    int rc = bse_create(&sc, c->device, c->budget);
+    if (rc != BSE_OK) {
+      for (auto* x : S->slot_ctx) bse_destroy(x);
+      delete S;
+      return rc;
+    }
+    S->slot_ctx.push_back(sc);
+  }
+  for (int i = 0; i < slots; ++i) S->workers.emplace_back(worker_main, S, S->slot_ctx[i]);
+  c->serve = S;
+  return BSE_OK;
+}
+
+extern "C" int bse_submit(bse_ctx* c, const bse_request* req, uint64_t* ticket) {
+  if (!c || !req || !ticket || req->n < 1 || !req->A || !req->B || !req->lambda) return BSE_ERR_ARG;
+  if (req->precision < BSE_FP64 || req->precision > BSE_MIXED_REFINED) return BSE_ERR_ARG;
+  ServeState* S = c->serve;
+  if (!S) {
+    record_message("bse_submit: call bse_serve_start first");
+    return BSE_ERR_ARG;
+  }
+  Pending p;
+  p.req = *req;
+  p.bytes = request_bytes(*req);
+  if (p.bytes > S->budget) {
+    record_message("bse_submit: request exceeds the HBM budget");
+    return BSE_ERR_NOMEM;
+  }
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) return BSE_ERR_ARG;
+    if (S->queue.size() >= S->queue_cap) return BSE_ERR_BUSY;
+    p.ticket = S->next_ticket++;
+    p.t_submit = S->now();
+    S->known[p.ticket] = true;
+    S->queue.push_back(p);
+  }
+  S->cv.notify_one();
+  *ticket = p.ticket;
+  return BSE_OK;
+}
+
+extern "C" int bse_poll(bse_ctx* c, uint64_t ticket, bse_result* res, int* done) {
+  if (!c || !done) return BSE_ERR_ARG;
+  ServeState* S = c->serve;
+  if (!S) return BSE_ERR_NO_TICKET;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (!S->known.count(ticket)) return BSE_ERR_NO_TICKET;
+  auto it = S->done.find(ticket);
+  if (it == S->done.end()) {
+    *done = 0;
+    return BSE_OK;
+  }
+  *done = 1;
+  if (res) *res = it->second;
+  S->done.erase(it);
+  S->known.erase(ticket);
+  return BSE_OK;
+}
+
+extern "C" int bse_serve_stop(bse_ctx* c, double timeout_s) {
+  if (!c) return BSE_ERR_ARG;
+  ServeState* S = c->serve;
+  if (!S) return BSE_OK;
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+  bool drained = false;
+  for (;;) {
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      if (S->queue.empty() && S->running == 0) {
+        drained = true;
+      }
+      if (drained || std::chrono::steady_clock::now() > deadline) {
+        S->stop = true;
+        if (!drained) S->queue.clear();
+        break;
+      }
+    }
+    std::this_thread::sleep_for(std::chrono::milliseconds(5));
+  }
+  S->cv.notify_all();
+  for (auto& t : S->workers) t.join();
+  for (auto* x : S->slot_ctx) bse_destroy(x);
+  delete S;
+  c->serve = nullptr;
+  return drained ? BSE_OK : BSE_ERR_TIMEOUT;
+}
+
+extern "C" int bse_solve_batched(bse_ctx* c, int count, const int* ns, const double* const* A,
+                                 const double* const* B, int precision, double* const* lambdas, double* const* Xs,
+                                 int* statuses) {
+  if (!c || count < 0 || (count > 0 && (!ns || !A || !B || !lambdas))) return BSE_ERR_ARG;
+  int first_err = BSE_OK;
+  for (int i = 0; i < count; ++i) {
+    int rc = bse_solve(c, ns[i], A[i], ns[i], B[i], ns[i], precision, lambdas[i], Xs ? Xs[i] : nullptr, nullptr,
+                       nullptr, nullptr);
+    if (statuses) statuses[i] = rc;
+    if (rc != BSE_OK && first_err == BSE_OK) first_err = rc;
+  }
+  return first_err;
+}

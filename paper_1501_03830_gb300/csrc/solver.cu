@@ -1,0 +1,418 @@
+// Host side of the C ABI: contexts, workspace cache, bse_solve / bse_spectrum.
+//
+// bse_solve runs Algorithm 1 with Algorithm 3 for its steps 4-5, every stage a
+// kernel of this library on the context's stream:
+//   form M -> Cholesky -> W -> skew tridiagonal reduction -> tridiagonal
+//   eigensolve -> back-transform (-> FP64 refinement) (-> weights on request)
+// Inputs and outputs may live on the host or the device; host data is staged
+// through the workspace with one cudaMemcpyAsync per buffer.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.cuh"
+#include "solver.h"
+
+namespace bse {
+
+static thread_local std::string g_last_error;
+
+void record_error(const char* what, cudaError_t err, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(err), file, line);
+  g_last_error = buf;
+}
+void record_message(const char* msg) { g_last_error = msg; }
+
+static inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t workspace_bytes(int n, int precision) {
+  const size_t m = 2 * (size_t)n;
+  const bool f32 = precision != BSE_FP64;
+  const size_t ts = f32 ? 4 : 8;
+  size_t b = 0;
+  b += 2 * al256(16 * (size_t)n * n);         // A, B staging
+  b += al256(8 * m * m);                       // M (FP64)
+  if (f32) b += al256(4 * m * m);              // L (FP32)
+  b += al256(ts * m * m);                      // W
+  b += al256(8 * m) + al256(ts * m) + al256(8 * (size_t)n);  // e, tau, lambda
+  b += al256(8 * m * n);                       // Vs
+  b += 2 * al256(16 * m * n);                  // X, Y
+  b += al256(64);                              // status
+  size_t scratch = f32 ? potrf_worksize<float>((int)m) : potrf_worksize<double>((int)m);
+  scratch = std::max(scratch, f32 ? trd_worksize<float>((int)m) : trd_worksize<double>((int)m));
+  scratch = std::max(scratch, sizeof(double) * (m + 8));
+  scratch = std::max(scratch, f32 ? bt_worksize<float>((int)m) : bt_worksize<double>((int)m));
+  if (precision == BSE_MIXED_REFINED) scratch = std::max(scratch, refine_worksize(n));
+  b += al256(scratch);
+  return b;
+}
+
+int Workspace::init(int n_, int precision_) {
+  n = n_;
+  precision = precision_;
+  const size_t m = 2 * (size_t)n;
+  const bool f32 = precision != BSE_FP64;
+  const size_t ts = f32 ? 4 : 8;
+  bytes = workspace_bytes(n, precision);
+  cudaError_t err = cudaMalloc(&base, bytes);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    base = nullptr;
+    record_error("cudaMalloc(workspace)", err, __FILE__, __LINE__);
+    return BSE_ERR_NOMEM;
+  }
+  char* p = (char*)base;
+  auto take = [&](size_t sz) {
+    void* r = p;
+    p += al256(sz);
+    return r;
+  };
+  A = (double*)take(16 * (size_t)n * n);
+  B = (double*)take(16 * (size_t)n * n);
+  M = (double*)take(8 * m * m);
+  Lf = f32 ? (float*)take(4 * m * m) : nullptr;
+  W = take(ts * m * m);
+  e = (double*)take(8 * m);
+  tau = take(ts * m);
+  lam = (double*)take(8 * (size_t)n);
+  Vs = (double*)take(8 * m * n);
+  X = (double*)take(16 * m * n);
+  Y = (double*)take(16 * m * n);
+  status = (DevStatus*)take(64);
+  scratch = p;
+  return BSE_OK;
+}
+
+void Workspace::release() {
+  if (base) cudaFree(base);
+  base = nullptr;
+}
+
+}  // namespace bse
+
+using namespace bse;
+
+static const char* kVersion = "bse-gb300 0.1 (sm_103a)";
+
+extern "C" const char* bse_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char* bse_version(void) { return kVersion; }
+
+extern "C" int bse_create(bse_ctx** out, int device, size_t hbm_budget) {
+  if (!out) return BSE_ERR_ARG;
+  *out = nullptr;
+  int count = 0;
+  BSE_CUDA(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) {
+    record_message("bse_create: no such CUDA device");
+    return BSE_ERR_ARG;
+  }
+  BSE_CUDA(cudaSetDevice(device));
+  bse_ctx* c = new bse_ctx();
+  c->device = device;
+  size_t fr = 0, tot = 0;
+  BSE_CUDA(cudaMemGetInfo(&fr, &tot));
+  c->budget = hbm_budget ? hbm_budget : (size_t)(0.9 * (double)fr);
+  if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    record_message("bse_create: cudaStreamCreate failed");
+    return BSE_ERR_CUDA;
+  }
+  c->stream = c->own_stream;
+  for (int i = 0; i < 12; ++i) cudaEventCreate(&c->ev[i]);
+  *out = c;
+  return BSE_OK;
+}
+
+extern "C" int bse_destroy(bse_ctx* c) {
+  if (!c) return BSE_OK;
+  bse_serve_stop(c, 60.0);
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->ws) kv.second.release();
+  c->ws.clear();
+  for (int i = 0; i < 12; ++i) cudaEventDestroy(c->ev[i]);
+  cudaStreamDestroy(c->own_stream);
+  delete c;
+  return BSE_OK;
+}
+
+extern "C" int bse_set_stream(bse_ctx* c, void* stream) {
+  if (!c) return BSE_ERR_ARG;
+  c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+  return BSE_OK;
+}
+
+extern "C" int bse_set_timing(bse_ctx* c, int on) {
+  if (!c) return BSE_ERR_ARG;
+  c->timing = on != 0;
+  return BSE_OK;
+}
+
+namespace bse {
+
+size_t ctx_bytes_held(bse_ctx* c) {
+  size_t s = 0;
+  for (auto& kv : c->ws) s += kv.second.bytes;
+  return s;
+}
+
+int get_workspace(bse_ctx* c, int n, int precision, Workspace** out) {
+  const long key = (long)n * 4 + precision;
+  auto it = c->ws.find(key);
+  if (it != c->ws.end()) {
+    it->second.last_use = ++c->use_clock;
+    *out = &it->second;
+    return BSE_OK;
+  }
+  const size_t need = workspace_bytes(n, precision);
+  if (need > c->budget) {
+    record_message("workspace exceeds the context's HBM budget");
+    return BSE_ERR_NOMEM;
+  }
+  // evict least recently used workspaces until the new one fits the budget
+  while (ctx_bytes_held(c) + need > c->budget && !c->ws.empty()) {
+    auto victim = c->ws.begin();
+    for (auto i = c->ws.begin(); i != c->ws.end(); ++i)
+      if (i->second.last_use < victim->second.last_use) victim = i;
+    cudaStreamSynchronize(c->stream);
+    victim->second.release();
+    c->ws.erase(victim);
+  }
+  Workspace w;
+  int rc = w.init(n, precision);
+  if (rc != BSE_OK) return rc;
+  w.last_use = ++c->use_clock;
+  c->ws[key] = w;
+  *out = &c->ws[key];
+  return BSE_OK;
+}
+
+static int copy_in(const double* src, int ld, int n, double* dst, cudaStream_t s, const double** used, int* ldu) {
+  if (is_device_ptr(src)) {
+    *used = src;
+    *ldu = ld;
+    return BSE_OK;
+  }
+  BSE_CUDA(cudaMemcpy2DAsync(dst, (size_t)n * 16, src, (size_t)ld * 16, (size_t)n * 16, n, cudaMemcpyHostToDevice, s));
+  *used = dst;
+  *ldu = n;
+  return BSE_OK;
+}
+
+__global__ void negate_bottom_kernel(int n, double2* Y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= n) return;
+  double2* p = Y + n + i + (long)j * 2 * n;
+  double2 v = *p;
+  *p = make_double2(-v.x, -v.y);
+}
+
+int negate_bottom(int n, double* Y, cudaStream_t s) {
+  negate_bottom_kernel<<<dim3(ceil_div(n, 256), n), 256, 0, s>>>(n, reinterpret_cast<double2*>(Y));
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
+// Runs the whole pipeline on device-resident inputs into the workspace outputs
+// (ws->lam, ws->X, ws->Y). Stage events go to ev[0..8] when timing.
+int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, const double* dB, int ldb,
+                 int precision, bool want_Y, bse_info* info, cudaStream_t s) {
+  const int m = 2 * n;
+  cudaEvent_t* ev = c->ev;
+  const bool tm = c->timing;
+  BSE_CUDA(cudaMemsetAsync(ws->status, 0, sizeof(DevStatus), s));
+  if (tm) cudaEventRecord(ev[0], s);
+  const bool f32 = precision != BSE_FP64;
+  BSE_TRY(form_M(n, dA, lda, dB, ldb, ws->M, m, f32 ? ws->Lf : nullptr, m, s));
+  if (tm) cudaEventRecord(ev[1], s);
+  if (!f32) {
+    double* W = (double*)ws->W;
+    double* tau = (double*)ws->tau;
+    BSE_TRY(potrf<double>(m, ws->M, m, ws->scratch, ws->status, s));
+    if (tm) cudaEventRecord(ev[2], s);
+    BSE_TRY(form_W<double>(n, ws->M, m, W, m, s));
+    if (tm) cudaEventRecord(ev[3], s);
+    BSE_TRY(tridiagonalize<double>(m, W, m, ws->e, tau, ws->scratch, s));
+    if (tm) cudaEventRecord(ev[4], s);
+    BSE_TRY(tdeig(m, ws->e, ws->lam, ws->Vs, (double*)ws->scratch, ws->status, s));
+    if (tm) cudaEventRecord(ev[5], s);
+    BSE_TRY(backtransform<double>(m, ws->M, m, W, m, tau, ws->Vs, ws->lam, ws->X, want_Y ? ws->Y : nullptr, m,
+                                  ws->scratch, s));
+    if (tm) cudaEventRecord(ev[6], s);
+  } else {
+    float* W = (float*)ws->W;
+    float* tau = (float*)ws->tau;
+    BSE_TRY(potrf<float>(m, ws->Lf, m, ws->scratch, ws->status, s));
+    if (tm) cudaEventRecord(ev[2], s);
+    BSE_TRY(form_W<float>(n, ws->Lf, m, W, m, s));
+    if (tm) cudaEventRecord(ev[3], s);
+    BSE_TRY(tridiagonalize<float>(m, W, m, ws->e, tau, ws->scratch, s));
+    if (tm) cudaEventRecord(ev[4], s);
+    BSE_TRY(tdeig(m, ws->e, ws->lam, ws->Vs, (double*)ws->scratch, ws->status, s));
+    if (tm) cudaEventRecord(ev[5], s);
+    const bool refine_now = precision == BSE_MIXED_REFINED;
+    BSE_TRY(backtransform<float>(m, ws->Lf, m, W, m, tau, ws->Vs, ws->lam, ws->X,
+                                 (want_Y && !refine_now) ? ws->Y : nullptr, m, ws->scratch, s));
+    if (tm) cudaEventRecord(ev[6], s);
+    if (refine_now) {
+      int sweeps = 0;
+      double resid = 0, dl = 0, dl0 = 0;
+      BSE_TRY(refine(n, ws->M, ws->lam, ws->X, 3, 0.0, ws->scratch, ws->status, s, &sweeps, &resid, &dl, &dl0));
+      if (info) {
+        info->sweeps = sweeps;
+        info->refine_resid = resid;
+        info->refine_dlam = dl;
+        info->unrefined_dlam = dl0;
+      }
+      if (want_Y) {
+        // Y = diag(I, -I) X
+        BSE_CUDA(cudaMemcpyAsync(ws->Y, ws->X, (size_t)16 * m * n, cudaMemcpyDeviceToDevice, s));
+        BSE_TRY(negate_bottom(n, ws->Y, s));
+      }
+    }
+  }
+  if (tm) cudaEventRecord(ev[7], s);
+  return BSE_OK;
+}
+
+static int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (!dst) return BSE_OK;
+  BSE_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+  return BSE_OK;
+}
+
+}  // namespace bse
+
+extern "C" int bse_solve(bse_ctx* c, int n, const double* A, int lda, const double* B, int ldb, int precision,
+                         double* lambda, double* X, double* Y, bse_sol** keep, bse_info* info) {
+  if (info) memset(info, 0, sizeof(*info));
+  // n <= 32767 keeps every per-column grid dimension (2n) within gridDim.y
+  if (!c || n < 1 || n > 32767 || !A || !B || lda < n || ldb < n) return BSE_ERR_ARG;
+  if (precision != BSE_FP64 && precision != BSE_MIXED && precision != BSE_MIXED_REFINED) return BSE_ERR_ARG;
+  if (keep) *keep = nullptr;
+  BSE_CUDA(cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  Workspace* ws = nullptr;
+  BSE_TRY(get_workspace(c, n, precision, &ws));
+  const int m = 2 * n;
+  if (c->timing) cudaEventRecord(c->ev[8], s);
+  const double *dA, *dB;
+  int la, lb;
+  BSE_TRY(copy_in(A, lda, n, ws->A, s, &dA, &la));
+  BSE_TRY(copy_in(B, ldb, n, ws->B, s, &dB, &lb));
+  if (c->timing) cudaEventRecord(c->ev[9], s);
+  int rc = run_pipeline(c, ws, n, dA, la, dB, lb, precision, Y != nullptr, info, s);
+  if (rc != BSE_OK) {
+    if (info) info->status = rc;
+    return rc;
+  }
+  DevStatus hst;
+  BSE_CUDA(cudaMemcpyAsync(&hst, ws->status, sizeof(hst), cudaMemcpyDeviceToHost, s));
+  BSE_TRY(copy_out(lambda, ws->lam, 8 * (size_t)n, s));
+  BSE_TRY(copy_out(X, ws->X, 16 * (size_t)m * n, s));
+  BSE_TRY(copy_out(Y, ws->Y, 16 * (size_t)m * n, s));
+  if (c->timing) cudaEventRecord(c->ev[10], s);
+  BSE_CUDA(cudaStreamSynchronize(s));
+  if (info) {
+    info->precision = precision;
+    info->status = hst.code;
+    info->info = hst.info;
+    if (c->timing) {
+      float ms = 0;
+      const int map[8] = {0, 1, 2, 3, 4, 5, 6, 7};
+      for (int k = 0; k < 7; ++k) {
+        cudaEventElapsedTime(&ms, c->ev[map[k]], c->ev[map[k + 1]]);
+        info->stage_ms[k] = ms;
+      }
+      // stage 5 (back-transform) ends at ev[6]; stage 6 (refinement) ends at ev[7]
+      cudaEventElapsedTime(&ms, c->ev[8], c->ev[9]);
+      float ms2 = 0;
+      cudaEventElapsedTime(&ms2, c->ev[7], c->ev[10]);
+      info->stage_ms[8] = ms + ms2;
+      cudaEventElapsedTime(&ms, c->ev[8], c->ev[10]);
+      info->stage_ms[9] = ms;
+    }
+  }
+  if (hst.code != 0) {
+    record_message(hst.code == BSE_ERR_NOT_DEFINITE ? "Eq. cond fails: Cholesky of M met a non-positive pivot"
+                                                    : "device-side failure");
+    return hst.code;
+  }
+  if (keep) {
+    bse_sol* sol = new bse_sol();
+    sol->n = n;
+    sol->device = c->device;
+    if (cudaMalloc(&sol->lam, 8 * (size_t)n) != cudaSuccess || cudaMalloc(&sol->X, 16 * (size_t)m * n) != cudaSuccess) {
+      cudaGetLastError();
+      bse_sol_free(sol);
+      record_message("bse_solve: cannot allocate the kept solution");
+      return BSE_ERR_NOMEM;
+    }
+    BSE_CUDA(cudaMemcpyAsync(sol->lam, ws->lam, 8 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    BSE_CUDA(cudaMemcpyAsync(sol->X, ws->X, 16 * (size_t)m * n, cudaMemcpyDeviceToDevice, s));
+    BSE_CUDA(cudaStreamSynchronize(s));
+    *keep = sol;
+  }
+  return BSE_OK;
+}
+
+extern "C" int bse_sol_view(const bse_sol* sol, int* n, const double** lambda_dev, const double** X_dev) {
+  if (!sol) return BSE_ERR_ARG;
+  if (n) *n = sol->n;
+  if (lambda_dev) *lambda_dev = sol->lam;
+  if (X_dev) *X_dev = sol->X;
+  return BSE_OK;
+}
+
+extern "C" int bse_sol_free(bse_sol* sol) {
+  if (!sol) return BSE_OK;
+  if (sol->lam) cudaFree(sol->lam);
+  if (sol->X) cudaFree(sol->X);
+  delete sol;
+  return BSE_OK;
+}
+
+extern "C" int bse_spectrum(bse_ctx* c, const bse_sol* sol, const double* d_r, const double* d_l, double* w) {
+  if (!c || !sol || !d_r || !d_l || !w) return BSE_ERR_ARG;
+  BSE_CUDA(cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  const int n = sol->n, m = 2 * n;
+  double* buf = nullptr;
+  const bool dr_dev = is_device_ptr(d_r), dl_dev = is_device_ptr(d_l), w_dev = is_device_ptr(w);
+  if (!dr_dev || !dl_dev || !w_dev) BSE_CUDA(cudaMallocAsync((void**)&buf, 16 * (size_t)(2 * m + n), s));
+  const double* dr = d_r;
+  const double* dl = d_l;
+  double* dw = w;
+  if (!dr_dev) {
+    BSE_CUDA(cudaMemcpyAsync(buf, d_r, 16 * (size_t)m, cudaMemcpyHostToDevice, s));
+    dr = buf;
+  }
+  if (!dl_dev) {
+    BSE_CUDA(cudaMemcpyAsync(buf + 2 * m, d_l, 16 * (size_t)m, cudaMemcpyHostToDevice, s));
+    dl = buf + 2 * m;
+  }
+  if (!w_dev) dw = buf + 4 * m;
+  int rc = weights(n, sol->X, m, dr, dl, dw, s);
+  if (rc == BSE_OK && !w_dev) BSE_CUDA(cudaMemcpyAsync(w, dw, 16 * (size_t)n, cudaMemcpyDeviceToHost, s));
+  if (buf) cudaFreeAsync(buf, s);
+  BSE_CUDA(cudaStreamSynchronize(s));
+  return rc;
+}

@@ -1,0 +1,61 @@
+// Host-side state behind the opaque bse_ctx / bse_sol handles.
+#pragma once
+
+#include <map>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace bse {
+
+struct Workspace {
+  int n = 0, precision = 0;
+  size_t bytes = 0;
+  unsigned long last_use = 0;
+  void* base = nullptr;
+  double *A = nullptr, *B = nullptr;  // staging for host inputs (complex128)
+  double* M = nullptr;                // FP64 M (L and then Phi on the FP64 path)
+  float* Lf = nullptr;                // FP32 copy of M -> L -> Phi (mixed paths)
+  void* W = nullptr;                  // W, then the reflectors (FP64 or FP32)
+  double* e = nullptr;                // sub-diagonal of T
+  void* tau = nullptr;
+  double* lam = nullptr;
+  double* Vs = nullptr;               // sign-folded V+ (row-major m x n)
+  double *X = nullptr, *Y = nullptr;  // complex128 2n x n
+  DevStatus* status = nullptr;
+  void* scratch = nullptr;            // stage scratch (max over stages)
+  int init(int n, int precision);
+  void release();
+};
+
+size_t workspace_bytes(int n, int precision);
+bool is_device_ptr(const void* p);
+
+struct ServeState;
+
+}  // namespace bse
+
+struct bse_ctx {
+  int device = 0;
+  size_t budget = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  bool timing = false;
+  cudaEvent_t ev[12];
+  std::map<long, bse::Workspace> ws;
+  unsigned long use_clock = 0;
+  bse::ServeState* serve = nullptr;
+};
+
+struct bse_sol {
+  int n = 0;
+  int device = 0;
+  double* lam = nullptr;
+  double* X = nullptr;
+};
+
+namespace bse {
+int get_workspace(bse_ctx* c, int n, int precision, Workspace** out);
+int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, const double* dB, int ldb,
+                 int precision, bool want_Y, bse_info* info, cudaStream_t s);
+}  // namespace bse

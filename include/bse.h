@@ -173,6 +173,25 @@ int bse_solve_batched(bse_ctx* ctx, int count, const int* ns, const double* cons
                       const double* const* B, int precision, double* const* lambdas,
                       double* const* Xs, int* statuses);
 
+/* ---- launch accounting and kernel timing -------------------------------- */
+/* Number of kernels this library has launched since it was loaded (all
+ * contexts and threads). */
+long long bse_launch_count(void);
+
+/* Kernel profiling: while on, each launch of a kernel class is bracketed by
+ * CUDA events on its stream and charged with the algorithmic bytes / flops of
+ * that launch (e.g. the skew SYMV: the strict lower triangle of the trailing
+ * matrix, once). Turning it on or off clears the totals. Adds event records to
+ * every launch: use it for an instrumented run, not a timed one. */
+int bse_kprof_enable(int on);
+
+/* Totals for kernel class k since profiling was turned on (synchronises on the
+ * recorded events): 0 form M, 1 Cholesky diagonal blocks, 2 FP64 GEMM, 3 FP32
+ * GEMM, 4 skew SYMV, 5 other tridiagonal-column kernels, 6 bisection,
+ * 7 tridiagonal eigenvectors, 8 weights, 9 elementwise, 10 tensor-core GEMM.
+ * BSE_ERR_ARG for an unknown class. */
+int bse_kprof_read(int k, long long* launches, double* ms, double* bytes, double* flops);
+
 /* Text of the last error recorded on this thread ("" if none). */
 const char* bse_last_error(void);
 

@@ -39,7 +39,7 @@ STAGE_NAMES = ["form_M", "cholesky", "form_W", "tridiag", "tdeig", "backtransfor
 EXPORTS = [
     "bse_create", "bse_destroy", "bse_set_stream", "bse_set_timing", "bse_solve", "bse_spectrum", "bse_sol_view",
     "bse_sol_free", "bse_serve_start", "bse_submit", "bse_poll", "bse_serve_stop", "bse_solve_batched",
-    "bse_last_error", "bse_version",
+    "bse_last_error", "bse_version", "bse_launch_count", "bse_kprof_enable", "bse_kprof_read",
     "bse_stage_form_M", "bse_stage_potrf_worksize", "bse_stage_potrf", "bse_stage_form_W",
     "bse_stage_tridiag_worksize", "bse_stage_tridiag", "bse_stage_tdeig_worksize", "bse_stage_tdeig",
     "bse_stage_backtransform_worksize", "bse_stage_backtransform", "bse_stage_weights",
@@ -101,6 +101,9 @@ def lib() -> C.CDLL:
         "bse_poll": (i, [vp, C.c_uint64, C.POINTER(bse_result), C.POINTER(i)]),
         "bse_serve_stop": (i, [vp, d]),
         "bse_solve_batched": (i, [vp, i, vp, vp, vp, i, vp, vp, vp]),
+        "bse_launch_count": (C.c_longlong, []),
+        "bse_kprof_enable": (i, [i]),
+        "bse_kprof_read": (i, [i, C.POINTER(C.c_longlong), C.POINTER(d), C.POINTER(d), C.POINTER(d)]),
         "bse_last_error": (C.c_char_p, []),
         "bse_version": (C.c_char_p, []),
         "bse_stage_form_M": (i, [i, vp, i, vp, i, vp, i, vp, i, vp]),
@@ -284,6 +287,29 @@ def make_request(n, A, B, lam, X=None, d_r=None, d_l=None, w=None, precision="mi
     r.X = ptr(X)
     r.w = ptr(w)
     return r
+
+
+KPROF_CLASSES = ["form_M", "potrf_diag", "gemm_f64", "gemm_f32", "trd_symv", "trd_col", "tdeig_bisect",
+                 "tdeig_vec", "weights", "elementwise", "gemm_tc"]
+
+
+def launch_count() -> int:
+    return int(lib().bse_launch_count())
+
+
+def kprof_enable(on: bool) -> None:
+    check(lib().bse_kprof_enable(int(on)), "bse_kprof_enable")
+
+
+def kprof_read() -> dict:
+    """Per kernel class: launches, device ms, charged bytes and flops."""
+    out = {}
+    for k, name in enumerate(KPROF_CLASSES):
+        n = C.c_longlong()
+        ms, b, f = C.c_double(), C.c_double(), C.c_double()
+        check(lib().bse_kprof_read(k, C.byref(n), C.byref(ms), C.byref(b), C.byref(f)), "bse_kprof_read")
+        out[name] = {"launches": n.value, "ms": ms.value, "bytes": b.value, "flops": f.value}
+    return out
 
 
 def version() -> str:

@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include "../../include/bse.h"
+#include "kprof.cuh"
 
 namespace bse {
 

@@ -11,6 +11,12 @@ static int launch_gemm(const GemmArgs& g, cudaStream_t s) {
   constexpr int NT = (BM / TM) * (BN / TN);
   long tiles = (long)ceil_div(g.M, BM) * ceil_div(g.N, BN);
   dim3 grid((unsigned)tiles, 1, (unsigned)(g.batch > 0 ? g.batch : 1));
+  // charged flops: 2MNK, halved for a triangular output and for each triangular operand
+  double fl = 2.0 * g.M * g.N * (double)g.K * (g.batch > 0 ? g.batch : 1);
+  if (g.c_uplo) fl *= 0.5;
+  if (g.a_tri) fl *= 0.5;
+  if (g.b_tri) fl *= 0.5;
+  KprofScope ks(sizeof(T) == 8 ? K_GEMM_F64 : K_GEMM_F32, s, 0.0, fl);
   if (!g.transA && !g.transB)
     gemm_simt_kernel<T, BM, BN, BK, TM, TN, false, false><<<grid, NT, 0, s>>>(g);
   else if (!g.transA && g.transB)

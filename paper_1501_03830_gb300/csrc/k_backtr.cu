@@ -129,17 +129,26 @@ int backtransform(int m, T* L, long ldl, const T* W, long ldw, const T* tau, con
                   const double* lam, double* X, double* Y, long ldx, void* work, cudaStream_t s) {
   const int n = m / 2;
   BtWork<T> w = carve_bt<T>(work, m);
-  bt_zero_upper<T><<<dim3(ceil_div(m, 256), m), 256, 0, s>>>(m, L, ldl);
+  {
+    KprofScope ks(K_ELEMENTWISE, s, 0.5 * sizeof(T) * m * (double)m, 0.0);
+    bt_zero_upper<T><<<dim3(ceil_div(m, 256), m), 256, 0, s>>>(m, L, ldl);
+  }
   BSE_LAUNCH_CHECK();
   const int nref = m - 1;  // reflectors j = 0..m-2 act on rows/cols j+1..m-1
   for (int j0 = 0; j0 < nref; j0 += BT_NB) {
     const int nbp = min(BT_NB, nref - j0);
     const int rows = m - j0 - 1;
-    bt_copy_panel<T><<<dim3(ceil_div(m, 256), BT_NB), 256, 0, s>>>(m, j0, nbp, W, ldw, w.Vb);
+    {
+      KprofScope ks(K_ELEMENTWISE, s, 2.0 * sizeof(T) * m * BT_NB, 0.0);
+      bt_copy_panel<T><<<dim3(ceil_div(m, 256), BT_NB), 256, 0, s>>>(m, j0, nbp, W, ldw, w.Vb);
+    }
     BSE_LAUNCH_CHECK();
     // G = V^T V
     BSE_TRY(gemm<T>(nbp, nbp, rows, 1.0, w.Vb + j0 + 1, m, true, w.Vb + j0 + 1, m, false, 0.0, w.G, BT_NB, s));
-    bt_larft<T><<<1, BT_NB, 0, s>>>(nbp, w.G, tau + j0, w.Tf);
+    {
+      KprofScope ks(K_ELEMENTWISE, s, 0.0, 0.0);
+      bt_larft<T><<<1, BT_NB, 0, s>>>(nbp, w.G, tau + j0, w.Tf);
+    }
     BSE_LAUNCH_CHECK();
     T* Phi = L + (long)(j0 + 1) * ldl;  // columns j0+1..m-1
     // Z = Phi V ; Z2 = Z T ; Phi -= Z2 V^T
@@ -149,7 +158,10 @@ int backtransform(int m, T* L, long ldl, const T* W, long ldw, const T* tau, con
   }
   const T* Vsx;
   if (sizeof(T) == 4) {
-    to_float_kernel<T><<<1024, 256, 0, s>>>((long)m * n, Vs, w.Vsf);
+    {
+      KprofScope ks(K_ELEMENTWISE, s, 12.0 * m * (double)n, 0.0);
+      to_float_kernel<T><<<1024, 256, 0, s>>>((long)m * n, Vs, w.Vsf);
+    }
     BSE_LAUNCH_CHECK();
     Vsx = w.Vsf;
   } else {
@@ -158,8 +170,11 @@ int backtransform(int m, T* L, long ldl, const T* W, long ldw, const T* tau, con
   // F_re = Phi[:, even] Vs[even, :],  F_im = Phi[:, odd] Vs[odd, :]
   BSE_TRY(gemm<T>(m, n, n, 1.0, L, 2 * ldl, false, Vsx, 2L * n, true, 0.0, w.Fre, m, s));
   BSE_TRY(gemm<T>(m, n, n, 1.0, L + ldl, 2 * ldl, false, Vsx + n, 2L * n, true, 0.0, w.Fim, m, s));
-  bt_epilogue<T><<<dim3(ceil_div(n, 128), n), 128, 0, s>>>(n, w.Fre, w.Fim, m, lam, reinterpret_cast<double2*>(X),
-                                                            reinterpret_cast<double2*>(Y), ldx);
+  {
+    KprofScope ks(K_ELEMENTWISE, s, 2.0 * sizeof(T) * m * (double)n + 32.0 * m * (double)n, 0.0);
+    bt_epilogue<T><<<dim3(ceil_div(n, 128), n), 128, 0, s>>>(n, w.Fre, w.Fim, m, lam, reinterpret_cast<double2*>(X),
+                                                              reinterpret_cast<double2*>(Y), ldx);
+  }
   BSE_LAUNCH_CHECK();
   return BSE_OK;
 }

@@ -73,6 +73,7 @@ int form_M(int n, const double* A, int lda, const double* B, int ldb, double* M,
            int ldmf, cudaStream_t s) {
   if (n <= 0) return BSE_OK;
   dim3 grid(ceil_div(n, 32), ceil_div(n, 32));
+  KprofScope ks(K_FORM_M, s, 32.0 * n * n + 32.0 * n * n + (Mf ? 16.0 * n * n : 0.0), 0.0);
   form_M_kernel<<<grid, dim3(32, 8), 0, s>>>(n, reinterpret_cast<const double2*>(A), lda,
                                              reinterpret_cast<const double2*>(B), ldb, M, ldm, Mf, ldmf);
   BSE_LAUNCH_CHECK();

@@ -46,7 +46,10 @@ int form_W(int n, const T* L, long ldl, T* W, long ldw, cudaStream_t s) {
   // C = L11^T L21   (op(A)(i,k) = L11(k,i): zero for k < i)
   BSE_TRY(gemm<T>(n, n, n, 1.0, L11, ldl, true, L21, ldl, false, 0.0, Cs, ldw, s, TRI_UPPER, TRI_NONE, 0));
   dim3 grid(ceil_div(n, 32), ceil_div(n, 32));
-  skew_from_C_kernel<T><<<grid, dim3(32, 8), 0, s>>>(n, W, ldw);
+  {
+    KprofScope ks(K_ELEMENTWISE, s, 2.0 * sizeof(T) * n * n, 0.0);
+    skew_from_C_kernel<T><<<grid, dim3(32, 8), 0, s>>>(n, W, ldw);
+  }
   BSE_LAUNCH_CHECK();
   // W21 = -L22^T L11  (op(A) upper: zero for k < i; op(B) = L11 lower: zero for k < j)
   BSE_TRY(gemm<T>(n, n, n, -1.0, L22, ldl, true, L11, ldl, false, 0.0, W + n, ldw, s, TRI_UPPER, TRI_LOWER, 0));

@@ -88,7 +88,10 @@ int potrf(int m, T* A, long lda, void* work, DevStatus* st, cudaStream_t s) {
   for (int k0 = 0; k0 < m; k0 += POTRF_NB) {
     const int kb = min(POTRF_NB, m - k0);
     T* Akk = A + k0 + (long)k0 * lda;
-    potf2_trtri_kernel<T><<<1, 256, 0, s>>>(kb, Akk, lda, Linv, k0, st);
+    {
+      KprofScope ks(K_POTRF_DIAG, s, 0.0, kb * (double)kb * kb / 3.0 + kb * (double)kb * kb / 3.0);
+      potf2_trtri_kernel<T><<<1, 256, 0, s>>>(kb, Akk, lda, Linv, k0, st);
+    }
     BSE_LAUNCH_CHECK();
     const int r = m - k0 - kb;
     if (r <= 0) break;

@@ -202,6 +202,7 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
   const int m = 2 * n;
   RefWork w = carve_ref(work, n);
   const dim3 eg(ceil_div(n, 128), n);
+  kcount(2);
   ref_x_to_u<<<eg, 128, 0, s>>>(n, reinterpret_cast<const double2*>(X), w.Ur, w.Ui);
   BSE_LAUNCH_CHECK();
   BSE_CUDA(cudaMemsetAsync(w.scal, 0, 64, s));
@@ -222,6 +223,7 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     BSE_TRY(gemm<double>(m, n, m, 1.0, M, m, false, w.Ur, m, false, 0.0, w.Pr, m, s));
     BSE_TRY(gemm<double>(m, n, m, 1.0, M, m, false, w.Ui, m, false, 0.0, w.Pi, m, s));
     BSE_CUDA(cudaMemsetAsync(w.maxes, 0, 16, s));
+    kcount(1);
     ref_colstats<<<n, 256, 0, s>>>(n, w.Ur, w.Ui, w.Pr, w.Pi, lam, w.lam_new, w.bnorm, w.scal, w.maxes);
     BSE_LAUNCH_CHECK();
     unsigned long long hm[2];
@@ -239,6 +241,7 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     BSE_TRY(gemm<double>(n, n, m, 1.0, w.Ur, m, true, w.Pi, m, false, 0.0, w.G3, n, s));
     BSE_TRY(gemm<double>(n, n, m, 1.0, w.Ui, m, true, w.Pr, m, false, 0.0, w.G4, n, s));
     const double gap_tol = fmax(1e-14, 4.0 * dl);
+    kcount(1);
     ref_buildE<<<eg, 128, 0, s>>>(n, w.G1, w.G2, w.G3, w.G4, lam, w.bnorm, gap_tol, w.Fa, w.Fb, w.Fc, w.Fd);
     BSE_LAUNCH_CHECK();
     // V = U + Ur [Fa Fc] + Ui [Fb Fd]
@@ -252,6 +255,7 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     std::swap(w.Ui, w.Vi);
     ++sweeps;
   }
+  kcount(1);
   ref_u_to_x<<<eg, 128, 0, s>>>(n, w.Ur, w.Ui, reinterpret_cast<double2*>(X));
   BSE_LAUNCH_CHECK();
   *sweeps_done = sweeps;

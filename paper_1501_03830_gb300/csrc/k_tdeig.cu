@@ -170,14 +170,21 @@ int tdeig(int m, const double* e, double* lam, double* Vs, double* work, DevStat
   const int n = m / 2;
   double* e2 = work;
   double* scal = work + m;
-  tdeig_prep<<<1, 1024, 0, s>>>(m, e, e2, scal);
+  {
+    KprofScope ks(K_ELEMENTWISE, s, 16.0 * m, 0.0);
+    tdeig_prep<<<1, 1024, 0, s>>>(m, e, e2, scal);
+  }
   BSE_LAUNCH_CHECK();
-  tdeig_bisect<<<ceil_div(n, 32), 32, 0, s>>>(m, n, e2, scal, lam, st);
+  {
+    KprofScope ks(K_TDEIG_BISECT, s, 0.0, 0.0);
+    tdeig_bisect<<<ceil_div(n, 32), 32, 0, s>>>(m, n, e2, scal, lam, st);
+  }
   BSE_LAUNCH_CHECK();
   if (Vs) {
+    KprofScope ks(K_TDEIG_VEC, s, 7.0 * 8.0 * m * n, 0.0);
     tdeig_vectors<<<ceil_div(n, 32), 32, 0, s>>>(m, n, e, scal, lam, Vs);
-    BSE_LAUNCH_CHECK();
   }
+  BSE_LAUNCH_CHECK();
   return BSE_OK;
 }
 

@@ -270,15 +270,29 @@ int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStr
       const int j = j0 + c;
       const int rows = m - j - 1;
       const int g = ceil_div(rows, 256);
-      trd_colupdate<T><<<g, 256, 0, st>>>(m, j, c, W, ldw, w.VP, w.norm2);
-      trd_house<T><<<g, 256, 0, st>>>(m, j, c, W, ldw, w.VP, w.PV, w.norm2, w.dots, e, tau);
+      {
+        KprofScope ks(K_TRD_COL, st, 0.0, 0.0);
+        trd_colupdate<T><<<g, 256, 0, st>>>(m, j, c, W, ldw, w.VP, w.norm2);
+      }
+      {
+        KprofScope ks(K_TRD_COL, st, 0.0, 0.0);
+        trd_house<T><<<g, 256, 0, st>>>(m, j, c, W, ldw, w.VP, w.PV, w.norm2, w.dots, e, tau);
+      }
       const int s = j + 1;
       const int ns = ceil_div(m, TRD_TB) - s / TRD_TB;
       const int maxQ = ceil_div(ns, TRD_QC);
       const long items = (long)ns * maxQ;
-      trd_symv<T><<<(unsigned)ceil_div(items, 4), 128, 0, st>>>(m, s, W, ldw, w.VP + (long)c * m, w.Dpart,
-                                                               w.Tpart, ns, maxQ);
-      trd_finalize<T><<<g, 256, 0, st>>>(m, j, c, W, ldw, w.VP, w.PV, w.Dpart, w.Tpart, ns, maxQ, w.dots, tau);
+      {
+        // algorithmic traffic: the strict lower triangle of the trailing matrix, once
+        const double N = (double)(m - s);
+        KprofScope ks(K_TRD_SYMV, st, N * (N - 1.0) * 0.5 * sizeof(T), 2.0 * N * (N - 1.0));
+        trd_symv<T><<<(unsigned)ceil_div(items, 4), 128, 0, st>>>(m, s, W, ldw, w.VP + (long)c * m, w.Dpart,
+                                                                 w.Tpart, ns, maxQ);
+      }
+      {
+        KprofScope ks(K_TRD_COL, st, 0.0, 0.0);
+        trd_finalize<T><<<g, 256, 0, st>>>(m, j, c, W, ldw, w.VP, w.PV, w.Dpart, w.Tpart, ns, maxQ, w.dots, tau);
+      }
     }
     BSE_LAUNCH_CHECK();
     const int s2 = j0 + nbp;

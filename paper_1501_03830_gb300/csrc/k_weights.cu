@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(256) weights_kernel(int n, const double2* __re
 
 int weights(int n, const double* X, long ldx, const double* dr, const double* dl, double* w, cudaStream_t s) {
   if (n <= 0) return BSE_OK;
+  KprofScope ks(K_WEIGHTS, s, 32.0 * n * (double)n + 64.0 * n, 0.0);
   weights_kernel<<<n, 256, 0, s>>>(n, reinterpret_cast<const double2*>(X), ldx,
                                    reinterpret_cast<const double2*>(dr), reinterpret_cast<const double2*>(dl),
                                    reinterpret_cast<double2*>(w));

@@ -226,6 +226,7 @@ __global__ void negate_bottom_kernel(int n, double2* Y) {
 }
 
 int negate_bottom(int n, double* Y, cudaStream_t s) {
+  kcount(1);
   negate_bottom_kernel<<<dim3(ceil_div(n, 256), n), 256, 0, s>>>(n, reinterpret_cast<double2*>(Y));
   BSE_LAUNCH_CHECK();
   return BSE_OK;

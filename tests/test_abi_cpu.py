@@ -14,7 +14,7 @@ def _declared():
         with open(os.path.join(ROOT, "include", h)) as f:
             src = f.read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(bse_[A-Za-z0-9_]+)\s*\(", src, flags=re.M):
+        for m in re.finditer(r"^\s*(?:const\s+)?(?:[a-z_]+\s+)*[a-z_]+\s*\*?\s*(bse_[A-Za-z0-9_]+)\s*\(", src, flags=re.M):
             names.add(m.group(1))
     return names
 

@@ -63,6 +63,24 @@ int bse_stage_tridiag(int m, void* W, int ldw, double* e, void* tau, int fp32, v
 size_t bse_stage_tdeig_worksize(int m);
 int bse_stage_tdeig(int m, const double* e, double* lam, double* Vs, void* work, int* dev_status, void* stream);
 
+/* Allocation-free variant of bse_stage_tdeig (the paper has no counterpart: this
+ * is a packaging choice of this library). Same arguments and results, minus
+ * `work`: the scratch is a fixed 512 KiB array compiled into the library, so the
+ * call needs no device memory from the caller and allocates none itself (no
+ * cudaMalloc, no allocating library routine). It is for callers that cannot
+ * allocate device memory at the point of the call -- e.g. code that runs with a
+ * fixed, pre-reserved memory budget, or that is not allowed to synchronise the
+ * device the way cudaMalloc/cudaFree can.
+ *   - Limit: m <= 65536 (n <= 32768); larger m returns BSE_ERR_ARG with a message
+ *     in bse_last_error().
+ *   - The first call on a device looks up the array's device address (one
+ *     cudaGetSymbolAddress per device, with that device current); make that first
+ *     call before any stream capture.
+ *   - Every call on a device shares the one array and leaves its contents behind;
+ *     nothing in it needs clearing between calls, but calls that overlap on the GPU
+ *     (different streams, or host threads) race on it: serialise them. */
+int bse_stage_tdeig_noalloc(int m, const double* e, double* lam, double* Vs, int* dev_status, void* stream);
+
 /* Algorithm 3 steps 3-6 with the Lambda^{-1/2} of Algorithm 1 step 5:
  * Phi = L U (L overwritten by Phi), Y+ = Q Phi D V+, X = diag(I,-I) Y+ Lambda^{-1/2},
  * Y = diag(I,-I) X. L, W, tau: FP64 or FP32 (fp32); Vs, lam: FP64 as produced by

@@ -21,6 +21,8 @@
 // column and a warp touches 32 consecutive doubles per step.
 #include <float.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "../../include/bse_stages.h"
 
@@ -191,6 +193,56 @@ int tdeig(int m, const double* e, double* lam, double* Vs, double* work, DevStat
 }  // namespace bse
 
 extern "C" size_t bse_stage_tdeig_worksize(int m) { return sizeof(double) * ((size_t)m + 8); }
+
+// ---- allocation-free variant -------------------------------------------------
+// The eigensolver's scratch (alpha^2 for every off-diagonal entry plus a few
+// scalars) lives in a fixed array in the library's device image, so callers that
+// must not allocate device memory can still run this stage. The array exists on
+// every GPU that loads the library, until the process exits.
+constexpr int kTdeigNoAllocMaxM = 65536;  // m <= 65536 (n <= 32768): 512 KiB of doubles
+static __device__ __align__(256) double g_tdeig_scratch[kTdeigNoAllocMaxM + 8];
+
+static std::mutex g_tdeig_scratch_mu;
+static double* g_tdeig_scratch_dev[256];  // device address of the array, per device ordinal
+
+// Device address of the static scratch on the current device. The host-side
+// symbol is only a stand-in, so the address is looked up with
+// cudaGetSymbolAddress once per device (with that device current) and cached.
+static int tdeig_static_scratch(double** out) {
+  int dev = -1;
+  BSE_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) {
+    bse::record_message("bse_stage_tdeig_noalloc: device ordinal out of range");
+    return BSE_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_tdeig_scratch_mu);
+  if (!g_tdeig_scratch_dev[dev]) {
+    void* p = nullptr;
+    cudaError_t err = cudaGetSymbolAddress(&p, g_tdeig_scratch);
+    if (err != cudaSuccess || !p) {
+      bse::record_error("cudaGetSymbolAddress(g_tdeig_scratch)", err, __FILE__, __LINE__);
+      return BSE_ERR_CUDA;
+    }
+    g_tdeig_scratch_dev[dev] = static_cast<double*>(p);
+  }
+  *out = g_tdeig_scratch_dev[dev];
+  return BSE_OK;
+}
+
+extern "C" int bse_stage_tdeig_noalloc(int m, const double* e, double* lam, double* Vs, int* dev_status,
+                                       void* stream) {
+  if (m < 2 || (m & 1) || !e || !lam || !dev_status) return BSE_ERR_ARG;
+  if (m > kTdeigNoAllocMaxM) {
+    bse::record_message("bse_stage_tdeig_noalloc: m exceeds 65536, the size of its static scratch");
+    return BSE_ERR_ARG;
+  }
+  double* work = nullptr;
+  BSE_TRY(tdeig_static_scratch(&work));
+  // Every scratch value the kernels read is written earlier in the same call
+  // (tdeig_prep fills alpha^2 and the scalars), so stale contents from a
+  // previous call need no clearing.
+  return bse::tdeig(m, e, lam, Vs, work, reinterpret_cast<bse::DevStatus*>(dev_status), (cudaStream_t)stream);
+}
 
 extern "C" int bse_stage_tdeig(int m, const double* e, double* lam, double* Vs, void* work, int* dev_status,
                                void* stream) {

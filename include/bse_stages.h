@@ -50,9 +50,24 @@ int bse_stage_form_W(int n, const void* L, int ldl, void* W, int ldw, int fp32, 
 /* Algorithm 3 step 1 (remark 1): W = U T U^T by blocked skew-symmetric Householder
  * reduction, m = 2n. Reads W's strict lower triangle; on return e[k] = T[k+1,k]
  * (k = 0..m-2, FP64), tau[k] (FP64 or FP32 like W) and W[k+1:m, k] = v_k with
- * v_k[0] = 1 (H_k = I - tau_k v_k v_k^T, U = H_0 H_1 ... H_{m-2}). */
+ * v_k[0] = 1 (H_k = I - tau_k v_k v_k^T, U = H_0 H_1 ... H_{m-2}).
+ * Each 64-column panel is one cooperative launch whose grid barriers wait at most
+ * ~2 s; a barrier that gives up stores BSE_ERR_TIMEOUT in dev_status (the kernel
+ * returns, it never hangs). A failure already in dev_status skips the work. */
 size_t bse_stage_tridiag_worksize(int m, int fp32);
-int bse_stage_tridiag(int m, void* W, int ldw, double* e, void* tau, int fp32, void* work, void* stream);
+int bse_stage_tridiag(int m, void* W, int ldw, double* e, void* tau, int fp32, void* work, int* dev_status,
+                      void* stream);
+
+/* Diagnostics of the tridiagonal reduction (no counterpart in the paper):
+ * bse_debug_trace_tridiag makes every later bse_stage_tridiag / bse_solve record,
+ * for columns j < `columns`, the device clock (ns) of each block at five points
+ * of the column's work (before and after the first grid barrier, after the panel
+ * dot products, before and after the second barrier) into the device buffer
+ * (layout [column][5][block], unsigned 64-bit); NULL turns it off. The buffer must
+ * hold columns * 5 * bse_stage_tridiag_grid(m, fp32) entries. */
+int bse_debug_trace_tridiag(void* dev_buffer, int columns);
+/* Blocks in the cooperative grid of the panel kernel (the largest launched). */
+int bse_stage_tridiag_grid(int m, int fp32);
 
 /* Algorithm 3 step 2 (remark 2): positive eigenpairs of Tsym = -i D^H T D (zero
  * diagonal, off-diagonal -e[k]), D = diag(i^k), k = 0..m-1, m even. FP64.

@@ -34,7 +34,7 @@ struct Eps<float> {
   static constexpr float value = 1.1920929e-07f;
 };
 
-inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+__host__ __device__ inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 
 // Host error plumbing: the first CUDA error of a call is kept as text for
 // bse_last_error().

@@ -20,7 +20,7 @@ int form_W(int n, const T* L, long ldl, T* W, long ldw, cudaStream_t s);
 template <typename T>
 size_t trd_worksize(int m);
 template <typename T>
-int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStream_t st);
+int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStream_t st, DevStatus* status);
 
 int tdeig(int m, const double* e, double* lam, double* Vs, double* work, DevStatus* st, cudaStream_t s);
 

@@ -3,11 +3,11 @@
 // skew-symmetric level-2/level-3 kernels), blocked by NB = 64 columns.
 //
 // Column j (trailing matrix A_j = rows/cols j+1..m-1, skew):
-//   w   = column j of A_j              (pending panel updates applied: K1)
-//   H_j = I - tau v v^T, H_j w = beta e_1   (dlarfg convention: K2)
+//   w   = column j of A_j              (pending panel updates applied)
+//   H_j = I - tau v v^T, H_j w = beta e_1   (dlarfg convention)
 //   p   = tau A_j v                    (skew SYMV on the stored lower triangle
-//                                       of the panel-start matrix A0: K3, plus
-//                                       the panel's V (P^T v) - P (V^T v): K4)
+//                                       of the panel-start matrix A0, plus the
+//                                       panel's V (P^T v) - P (V^T v))
 //   A_{j+1} = H_j A_j H_j = A_j + v p^T - p v^T
 // (for skew A, v^T A v = 0, so the symmetric algorithm's correction term
 // vanishes). After NB columns the trailing lower triangle gets the rank-2NB
@@ -16,13 +16,15 @@
 // Outputs: beta_j (the sub-diagonal T[j+1, j]) in e[j], tau_j in tau[j], and
 // v_j in W[j+1:m, j] (with the explicit leading 1), j = 0..m-2.
 //
-// K3 is the HBM-bound kernel. One warp processes 32x32 sub-tiles of one
-// 32-row strip: lane l owns row r; the direct product sum_c A[r,c] v[c]
-// accumulates in a register, the transposed product -sum_r A[r,c] v[r] is
-// reduced across lanes with a 31-shuffle butterfly (lane l ends with column
-// c0 + l). Each stored element is read once per column (4m^3/3 bytes in
-// FP64 over the whole reduction). Partial sums go to two small buffers that
-// K4 reduces.
+// All NB columns of a panel run in one persistent cooperative launch with two
+// grid barriers per column (see trd_panel_kernel). The skew SYMV is the
+// HBM-bound part: one warp processes 32x32 sub-tiles of one 32-row strip; lane
+// l owns row r; the direct product sum_c A[r,c] v[c] accumulates in a register,
+// the transposed product -sum_r A[r,c] v[r] is reduced across lanes with a
+// 31-shuffle butterfly (lane l ends with column c0 + l), and the next
+// sub-tile's loads are in flight meanwhile. Each stored element is read once
+// per column (4m^3/3 bytes in FP64 over the whole reduction). Partial sums go
+// to two small buffers that the owners of the rows reduce after the barrier.
 #include "common.cuh"
 #include "gemm_simt.cuh"
 #include "../../include/bse_stages.h"
@@ -31,80 +33,51 @@ namespace bse {
 
 constexpr int TRD_NB = 64;   // panel width (the paper's n_b)
 constexpr int TRD_TB = 32;   // sub-tile edge = warp width
-constexpr int TRD_QC = 16;   // sub-tiles per warp work item
+constexpr int TRD_QC_MAX = 64;  // upper bound on sub-tiles per warp work item
 
 template <typename T>
 struct TrdWork {
   T* VP;        // m x 2NB: [V | P]
   T* PV;        // m x 2NB: [P | -V]
-  T* Dpart;     // direct partials   [ns][maxQ][32]
+  T* Dpart;     // direct partials   [ns][maxQ][32] (maxQ <= ns)
   T* Tpart;     // transposed partials [ns][ns][32]
-  double* norm2; // m
-  double* dots;  // m x 2NB: V^T v, P^T v per column
+  double* normpart;  // [kMaxGrid] per-block partial squared norms of the next column
+  double* dotpart;   // [kMaxGrid][2NB] per-block partial V^T v, P^T v
+  unsigned* bar;     // grid barrier words
 };
+
+constexpr int kMaxGrid = 1024;  // upper bound on the panel kernel's grid
 
 static inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 template <typename T>
 size_t trd_worksize(int m) {
   size_t ns = ceil_div(m, TRD_TB);
-  size_t maxQ = ceil_div((long)ns, TRD_QC);
+  size_t maxQ = ns;  // work items hold >= 1 sub-tile
   size_t b = 0;
   b += 2 * align256(sizeof(T) * (size_t)m * 2 * TRD_NB);
   b += align256(sizeof(T) * ns * maxQ * TRD_TB);
   b += align256(sizeof(T) * ns * ns * TRD_TB);
-  b += align256(sizeof(double) * (size_t)m);
-  b += align256(sizeof(double) * (size_t)m * 2 * TRD_NB);
+  b += align256(sizeof(double) * kMaxGrid);
+  b += align256(sizeof(double) * kMaxGrid * 2 * TRD_NB);
+  b += align256(64);
   return b;
 }
 
 template <typename T>
 static TrdWork<T> carve(void* work, int m) {
   size_t ns = ceil_div(m, TRD_TB);
-  size_t maxQ = ceil_div((long)ns, TRD_QC);
+  size_t maxQ = ns;
   char* p = reinterpret_cast<char*>(work);
   TrdWork<T> w;
   w.VP = reinterpret_cast<T*>(p); p += align256(sizeof(T) * (size_t)m * 2 * TRD_NB);
   w.PV = reinterpret_cast<T*>(p); p += align256(sizeof(T) * (size_t)m * 2 * TRD_NB);
   w.Dpart = reinterpret_cast<T*>(p); p += align256(sizeof(T) * ns * maxQ * TRD_TB);
   w.Tpart = reinterpret_cast<T*>(p); p += align256(sizeof(T) * ns * ns * TRD_TB);
-  w.norm2 = reinterpret_cast<double*>(p); p += align256(sizeof(double) * (size_t)m);
-  w.dots = reinterpret_cast<double*>(p);
+  w.normpart = reinterpret_cast<double*>(p); p += align256(sizeof(double) * kMaxGrid);
+  w.dotpart = reinterpret_cast<double*>(p); p += align256(sizeof(double) * kMaxGrid * 2 * TRD_NB);
+  w.bar = reinterpret_cast<unsigned*>(p);
   return w;
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// K1: apply the panel's pending updates to column j, accumulate ||w[1:]||^2.
-template <typename T>
-__global__ void __launch_bounds__(256) trd_colupdate(int m, int j, int c, T* __restrict__ W, long ldw,
-                                                     const T* __restrict__ VP, double* __restrict__ norm2) {
-  __shared__ double red[8];
-  const int r = j + 1 + blockIdx.x * 256 + threadIdx.x;
-  double sq = 0.0;
-  if (r < m) {
-    T w = W[r + (long)j * ldw];
-    for (int t = 0; t < c; ++t) {
-      const T vr = VP[r + (long)t * m], pr = VP[r + (long)(TRD_NB + t) * m];
-      const T vj = VP[j + (long)t * m], pj = VP[j + (long)(TRD_NB + t) * m];
-      w = fma(vr, pj, w);
-      w = fma(-pr, vj, w);
-    }
-    W[r + (long)j * ldw] = w;
-    if (r >= j + 2) sq = (double)w * (double)w;
-  }
-  sq = warp_sum(sq);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < 8; ++k) s += red[k];
-    if (s != 0.0) atomicAdd(norm2 + j, s);
-  }
 }
 
 struct House {
@@ -124,177 +97,540 @@ __device__ __forceinline__ House make_house(double alpha, double sigma) {
   return h;
 }
 
-// K2: Householder vector v (scaled in place), tau, beta; V^T v and P^T v.
 template <typename T>
-__global__ void __launch_bounds__(256) trd_house(int m, int j, int c, T* __restrict__ W, long ldw, T* VP,
-                                                 T* PV, const double* __restrict__ norm2,
-                                                 double* __restrict__ dots, double* __restrict__ e,
-                                                 T* __restrict__ tau_out) {
-  __shared__ double red[8][2 * TRD_NB];
-  const double alpha = (double)W[(j + 1) + (long)j * ldw];
-  const House h = make_house(alpha, norm2[j]);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    e[j] = h.beta;
-    tau_out[j] = (T)h.tau;
-  }
-  const int r = j + 1 + blockIdx.x * 256 + threadIdx.x;
-  double v = 0.0;
-  if (r < m) {
-    v = (r == j + 1) ? 1.0 : (double)W[r + (long)j * ldw] * h.scal;
-    const T vt = (T)v;
-    VP[r + (long)c * m] = vt;
-    PV[r + (long)(TRD_NB + c) * m] = -vt;
-    if (r > j + 1) W[r + (long)j * ldw] = vt;
-    v = (double)vt;
-  }
-  if (c == 0) return;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int t = 0; t < c; ++t) {
-    double a = 0.0, b = 0.0;
-    if (r < m) {
-      a = (double)VP[r + (long)t * m] * v;
-      b = (double)VP[r + (long)(TRD_NB + t) * m] * v;
-    }
-    a = warp_sum(a);
-    b = warp_sum(b);
-    if (lane == 0) {
-      red[wid][t] = a;
-      red[wid][TRD_NB + t] = b;
-    }
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < 2 * TRD_NB; q += 256) {
-    if ((q % TRD_NB) >= c) continue;
-    double s = 0.0;
-    for (int k = 0; k < 8; ++k) s += red[k][q];
-    if (s != 0.0) atomicAdd(dots + (long)j * 2 * TRD_NB + q, s);
-  }
+struct PanelArgs {
+  int m, j0, nbp;
+  T* W;
+  long ldw;
+  T* VP;
+  T* PV;
+  T* Dpart;
+  T* Tpart;
+  double* normpart;
+  double* dotpart;
+  double* e;
+  T* tau;
+  unsigned* bar;  // [0] arrivals, [1] generation
+  DevStatus* st;
+  int vec;  // 16-byte vector loads of W are aligned (ldw multiple of 16 B / sizeof(T), W 16-B aligned)
+  unsigned long long* trace;  // optional: [column][5 points][block] globaltimer stamps
+  int trace_cols;
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
-// K3: skew SYMV partials over the trailing matrix rows/cols [s, m) of A0 (the
-// stored strict lower triangle of W). 4 warps per CTA, one work item per warp.
 template <typename T>
-__global__ void __launch_bounds__(128) trd_symv(int m, int s, const T* __restrict__ W, long ldw,
-                                                const T* __restrict__ v, T* __restrict__ Dpart,
-                                                T* __restrict__ Tpart, int ns, int maxQ) {
-  const int lane = threadIdx.x & 31;
-  const long item = (long)blockIdx.x * 4 + (threadIdx.x >> 5);
-  const int Rr = (int)(item / maxQ), q = (int)(item % maxQ);
-  if (Rr >= ns) return;
-  const int cb0 = q * TRD_QC;
-  if (cb0 > Rr) return;
-  const int cb1 = min(cb0 + TRD_QC, Rr + 1);
-  const int sb = s / TRD_TB;
-  const int r = (sb + Rr) * TRD_TB + lane;
-  const bool rok = (r >= s) && (r < m);
-  const T vr = rok ? v[r] : T(0);
-  const T* Wr = W + (rok ? r : s);
-  T yd = T(0);
-  for (int cb = cb0; cb < cb1; ++cb) {
-    const int c0 = (sb + cb) * TRD_TB;
-    const bool diag = (cb == Rr);
-    T a[TRD_TB];
-#pragma unroll
-    for (int k = 0; k < TRD_TB; ++k) {
-      const int cc = c0 + k;
-      const bool ok = rok && cc >= s && cc < m && (!diag || cc < r);
-      a[k] = ok ? Wr[(long)cc * ldw] : T(0);
-    }
-#pragma unroll
-    for (int k = 0; k < TRD_TB; ++k) {
-      const int cc = c0 + k;
-      const T vc = (cc >= s && cc < m) ? v[cc] : T(0);
-      yd = fma(a[k], vc, yd);
-      a[k] *= vr;
-    }
-    // butterfly reduce-scatter: lane l ends with sum over lanes of a[l]
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-      const bool up = (lane & off) != 0;
-#pragma unroll
-      for (int k = 0; k < off; ++k) {
-        const T send = up ? a[k] : a[k + off];
-        const T keep = up ? a[k + off] : a[k];
-        a[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+__device__ __forceinline__ void trace_point(const PanelArgs<T>& a, int col, int point) {
+  if (a.trace && threadIdx.x == 0 && col < a.trace_cols)
+    a.trace[((long)col * 5 + point) * gridDim.x + blockIdx.x] = gtimer();
+}
+
+// Grid-wide barrier for a cooperative launch. The wait is bounded: after ~2 s
+// it records BSE_ERR_TIMEOUT and every block returns at its next barrier. A
+// failure recorded by any block (or an earlier stage) also makes all blocks
+// return.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, DevStatus* st) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long it = 0;
+      while (*vgen == g) {
+        if (++it > (1L << 25)) {
+          set_status(st, BSE_ERR_TIMEOUT, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(40);
       }
     }
-    // a[0] = sum_r A[r, c0+lane] v[r]: contributes -a[0] to y[c0+lane]
-    if (diag) {
-      yd -= a[0];
-    } else {
-      Tpart[((long)cb * ns + Rr) * TRD_TB + lane] = -a[0];
+    __threadfence();
+    if (*(volatile int*)&st->code != 0) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+  return __ldcg(p);
+}
+
+template <typename T>
+__device__ __forceinline__ double block_sum(double v, double* red8) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += red8[k];
+  return t;
+}
+
+// Butterfly reduce-scatter across the warp: on return a[0] of lane l holds the
+// sum over lanes of the input a[l].
+template <typename T>
+__device__ __forceinline__ void warp_reduce_scatter32(T (&a)[32], int lane) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < off; ++k) {
+      const T send = up ? a[k] : a[k + off];
+      const T keep = up ? a[k + off] : a[k];
+      a[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
     }
   }
-  Dpart[((long)Rr * maxQ + q) * TRD_TB + lane] = yd;
 }
 
-// K4: y = reduced partials; p = tau (y + V (P^T v) - P (V^T v)); store p.
-template <typename T>
-__global__ void __launch_bounds__(256) trd_finalize(int m, int j, int c, T* __restrict__ W, long ldw,
-                                                    T* VP, T* PV, const T* __restrict__ Dpart,
-                                                    const T* __restrict__ Tpart, int ns, int maxQ,
-                                                    const double* __restrict__ dots,
-                                                    const T* __restrict__ tau_in) {
-  const int s = j + 1;
-  const int r = s + blockIdx.x * 256 + threadIdx.x;
-  if (blockIdx.x == 0 && threadIdx.x == 0) W[(j + 1) + (long)j * ldw] = T(1);
-  if (r >= m) return;
-  const int sb = s / TRD_TB;
-  const int Rr = r / TRD_TB - sb, l = r % TRD_TB;
-  const int nq = (Rr + TRD_QC) / TRD_QC;  // ceil((Rr+1)/QC)
-  T y = T(0);
-  for (int q = 0; q < nq; ++q) y += Dpart[((long)Rr * maxQ + q) * TRD_TB + l];
-  for (int R2 = Rr + 1; R2 < ns; ++R2) y += Tpart[((long)Rr * ns + R2) * TRD_TB + l];
-  const double* d = dots + (long)j * 2 * TRD_NB;
-  for (int t = 0; t < c; ++t) {
-    y = fma(VP[r + (long)t * m], (T)d[TRD_NB + t], y);
-    y = fma(-VP[r + (long)(TRD_NB + t) * m], (T)d[t], y);
+// Sub-tiles per SYMV work item for a trailing matrix of ns strips: about one
+// non-empty item per warp of the grid, so no warp walks a long serial chain
+// when the matrix is small.
+__device__ __forceinline__ int symv_qc(int ns, int nwarps) {
+  const long tri = (long)ns * (ns + 1) / 2;
+  int qc = (int)((tri + 4L * nwarps - 1) / (4L * nwarps));  // about four items per warp
+  return max(1, min(qc, TRD_QC_MAX));
+}
+
+// Non-empty SYMV work items of strip R: floor(R/qc) + 1. items_before(R) counts
+// the items of strips 0..R-1, so a linear item index maps back to (strip, chunk)
+// by a binary search and every warp gets real work.
+__device__ __forceinline__ long items_before(int R, int qc) {
+  const long A = R / qc, B = R % qc;
+  return (long)R + (long)qc * (A * (A - 1) / 2) + A * B;
+}
+
+__device__ __forceinline__ void item_to_strip(long i, int ns, int qc, int* R, int* q) {
+  int lo = 0, hi = ns;  // items_before(lo) <= i < items_before(hi)
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (items_before(mid, qc) <= i) lo = mid;
+    else hi = mid;
   }
-  const T p = tau_in[j] * y;
-  VP[r + (long)(TRD_NB + c) * m] = p;
-  PV[r + (long)c * m] = p;
+  *R = lo;
+  *q = (int)(i - items_before(lo, qc));
 }
 
 template <typename T>
-int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStream_t st) {
+struct Vec;
+template <>
+struct Vec<float> {
+  using V = float4;
+  static constexpr int W = 4;
+  __device__ static void split(const V& x, float* o) { o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w; }
+};
+template <>
+struct Vec<double> {
+  using V = double2;
+  static constexpr int W = 2;
+  __device__ static void split(const V& x, double* o) { o[0] = x.x; o[1] = x.y; }
+};
+
+// Skew SYMV partials for one work item (strip Rr, column blocks cb0..cb1-1 of
+// the trailing matrix), processed by one warp. Lane (rg, cg) holds a VW x CPL
+// block of every 32x32 sub-tile: rows r0 + rg*VW + [0, VW) (one 16-byte vector
+// load per column) and columns c0 + cg*CPL + [0, CPL). Per element: one FMA for
+// A v and one for A^T v. The v values of a sub-tile's 32 columns are one
+// coalesced load (lane l: column c0 + l) shuffled to their users, and both the
+// tile and its v values are prefetched one sub-tile ahead. The transposed sums
+// are reduce-scattered over the RG lanes of a column group per sub-tile; the
+// direct sums stay in registers for the whole item and are reduce-scattered
+// over the CG lanes of a row group at its end. Sub-tiles on the diagonal or the
+// matrix edge take a masked scalar-load path.
+template <typename T>
+__device__ __forceinline__ void symv_item(const PanelArgs<T>& a, int j, int s, int sb, int ns, int maxQ, int Rr,
+                                          int cb0, int cb1, int q, T scal, int lane) {
+  constexpr int VW = Vec<T>::W;   // rows per lane
+  constexpr int RG = 32 / VW;     // lanes along the rows of a sub-tile
+  constexpr int CG = VW;          // column groups
+  constexpr int CPL = 32 / CG;    // columns per lane (= RG)
+  using V = typename Vec<T>::V;
+  const int m = a.m;
+  const long ldw = a.ldw;
+  const T* __restrict__ W = a.W;
+  const int rg = lane % RG, cg = lane / RG;
+  const int r0 = (sb + Rr) * TRD_TB;
+  const int rbase = r0 + rg * VW;
+  auto vval = [&](int idx) -> T {
+    return (idx >= s && idx < m) ? ((idx == s) ? T(1) : ldcg(W + idx + (long)j * ldw) * scal) : T(0);
+  };
+  T vr[VW];
+#pragma unroll
+  for (int i = 0; i < VW; ++i) vr[i] = vval(rbase + i);
+  const bool rows_full = (r0 >= s) && (r0 + TRD_TB <= m);
+  T yd[VW];
+#pragma unroll
+  for (int i = 0; i < VW; ++i) yd[i] = T(0);
+  T cur[CPL][VW], nxt[CPL][VW];
+  auto load_tile = [&](T (&dst)[CPL][VW], int cb) {
+    const int c0 = (sb + cb) * TRD_TB;
+    const int cbase = c0 + cg * CPL;
+    const bool fast = a.vec && rows_full && (cb != Rr) && (c0 >= s) && (c0 + TRD_TB <= m);
+    if (fast) {
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) {
+        const V x = *reinterpret_cast<const V*>(W + rbase + (long)(cbase + k) * ldw);
+        Vec<T>::split(x, dst[k]);
+      }
+    } else {
+      const bool diag = (cb == Rr);
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) {
+        const int cc = cbase + k;
+#pragma unroll
+        for (int i = 0; i < VW; ++i) {
+          const int r = rbase + i;
+          const bool ok = r >= s && r < m && cc >= s && cc < m && (!diag || cc < r);
+          dst[k][i] = ok ? W[r + (long)cc * ldw] : T(0);
+        }
+      }
+    }
+  };
+  load_tile(cur, cb0);
+  T vl = vval((sb + cb0) * TRD_TB + lane), vln = T(0);
+  for (int cb = cb0; cb < cb1; ++cb) {
+    if (cb + 1 < cb1) {
+      load_tile(nxt, cb + 1);
+      vln = vval((sb + cb + 1) * TRD_TB + lane);
+    }
+    T t[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+      const T vc = __shfl_sync(0xffffffffu, vl, cg * CPL + k);
+      T tk = T(0);
+#pragma unroll
+      for (int i = 0; i < VW; ++i) {
+        yd[i] = fma(cur[k][i], vc, yd[i]);
+        tk = fma(cur[k][i], vr[i], tk);
+      }
+      t[k] = tk;
+    }
+    // reduce-scatter over the RG lanes of this column group: lane rg ends with column cbase + rg
+#pragma unroll
+    for (int off = RG / 2; off >= 1; off >>= 1) {
+      const bool up = (rg & off) != 0;
+#pragma unroll
+      for (int k = 0; k < off; ++k) {
+        const T send = up ? t[k] : t[k + off];
+        const T keep = up ? t[k + off] : t[k];
+        t[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      }
+    }
+    // transposed contribution -sum_r A[r, c] v[r] to y[c]; the diagonal sub-tile's
+    // goes to the strip's own slot (cb == Rr), read back by the row owners
+    a.Tpart[((long)cb * ns + Rr) * TRD_TB + cg * CPL + rg] = -t[0];
+    if (cb + 1 < cb1) {
+      vl = vln;
+#pragma unroll
+      for (int k = 0; k < CPL; ++k)
+#pragma unroll
+        for (int i = 0; i < VW; ++i) cur[k][i] = nxt[k][i];
+    }
+  }
+  // direct sums: reduce-scatter over the CG lanes of a row group (shuffle
+  // distance RG): lane (rg, cg) ends with row rbase + cg
+#pragma unroll
+  for (int off = CG / 2; off >= 1; off >>= 1) {
+    const bool up = (cg & off) != 0;
+#pragma unroll
+    for (int i = 0; i < off; ++i) {
+      const T send = up ? yd[i] : yd[i + off];
+      const T keep = up ? yd[i + off] : yd[i];
+      yd[i] = keep + __shfl_xor_sync(0xffffffffu, send, off * RG);
+    }
+  }
+  a.Dpart[((long)Rr * maxQ + q) * TRD_TB + rg * VW + cg] = yd[0];
+}
+
+// One panel of the reduction (columns j0 .. j0+nbp-1) in one cooperative launch.
+// Per column j (panel index c), two grid barriers separate
+//   phase B/C: Householder scalars (every block, redundantly), the panel dot
+//              products V^T v, P^T v, and the skew SYMV partials of A0 v, with v
+//              formed on the fly from the unscaled column W[:, j];
+//   phase D+A: p = tau (A0 v + V (P^T v) - P (V^T v)) for the owned rows, v and p
+//              stored, then column j+1 updated with all pending panel terms and its
+//              squared norm accumulated.
+// Blocks own 256 consecutive rows counted from j+1; data written by other blocks
+// during the launch is read with __ldcg (L2) so no stale L1 line is used.
+template <typename T>
+__global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
+  __shared__ double red8[8];
+  __shared__ double dred[8][2 * TRD_NB];
+  const int m = a.m;
+  const long ldw = a.ldw;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nwarps = gridDim.x * 8;
+  const int gwarp = blockIdx.x * 8 + wid;
+  T* __restrict__ W = a.W;
+  T* VP = a.VP;
+  T* PV = a.PV;
+
+  // phase A for the first panel column: its norm (no pending updates yet)
+  {
+    const int j = a.j0;
+    const int r = j + 1 + blockIdx.x * 256 + tid;
+    double sq = 0.0;
+    if (r < m && r >= j + 2) {
+      const double w = (double)W[r + (long)j * ldw];
+      sq = w * w;
+    }
+    sq = block_sum<T>(sq, red8);
+    if (tid == 0) a.normpart[blockIdx.x] = sq;
+  }
+
+  for (int c = 0; c < a.nbp; ++c) {
+    const int j = a.j0 + c;
+    const int s = j + 1;
+    trace_point(a, j, 0);
+    if (!grid_barrier(a.bar, a.st)) return;
+    trace_point(a, j, 1);
+
+    // ---------------- phase B/C ----------------
+    const double alpha = (double)ldcg(W + (j + 1) + (long)j * ldw);
+    double sigma = 0.0;
+    for (int b = tid; b < (int)gridDim.x; b += 256) sigma += ldcg(a.normpart + b);
+    sigma = block_sum<T>(sigma, red8);  // the same order in every block
+    const House h = make_house(alpha, sigma);
+    const T scal = (T)h.scal;
+    if (blockIdx.x == 0 && tid == 0) {
+      a.e[j] = h.beta;
+      a.tau[j] = (T)h.tau;
+    }
+    const int r_own = s + blockIdx.x * 256 + tid;
+    // panel dot products over the owned rows
+    if (c > 0 && blockIdx.x * 256 + s < m) {
+      // in the path's own precision: FP64 arithmetic is a small fraction of the
+      // FP32 rate on this GPU and would dominate the column on the FP32 path
+      T vr = T(0);
+      if (r_own < m) vr = (r_own == s) ? T(1) : ldcg(W + r_own + (long)j * ldw) * scal;
+      T* tred = reinterpret_cast<T*>(&dred[0][0]);  // [8][2NB] in T
+      const int nq2 = 2 * c;
+      for (int q0 = 0; q0 < nq2; q0 += 32) {
+        T acc[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const int q = q0 + k;
+          T pv = T(0);
+          if (q < nq2 && r_own < m) {
+            const int col = q < c ? q : TRD_NB + (q - c);
+            pv = ldcg(VP + r_own + (long)col * m) * vr;
+          }
+          acc[k] = pv;
+        }
+        warp_reduce_scatter32<T>(acc, lane);
+        if (q0 + lane < nq2) tred[wid * 2 * TRD_NB + q0 + lane] = acc[0];
+      }
+      __syncthreads();
+      for (int q = tid; q < nq2; q += 256) {
+        T t = T(0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += tred[k * 2 * TRD_NB + q];
+        const int slot = q < c ? q : TRD_NB + (q - c);
+        a.dotpart[(long)blockIdx.x * 2 * TRD_NB + slot] = (double)t;
+      }
+    }
+    trace_point(a, j, 2);
+    // skew SYMV partials of A0[s:, s:] v
+    {
+      const int sb = s / TRD_TB;
+      const int ns = ceil_div(m, TRD_TB) - sb;
+      const int qc = symv_qc(ns, nwarps);
+      const int maxQ = (ns + qc - 1) / qc;
+      const long items = items_before(ns, qc);
+      for (long item = gwarp; item < items; item += nwarps) {
+        int Rr, q;
+        item_to_strip(item, ns, qc, &Rr, &q);
+        symv_item<T>(a, j, s, sb, ns, maxQ, Rr, q * qc, min(q * qc + qc, Rr + 1), q, scal, lane);
+      }
+    }
+    trace_point(a, j, 3);
+    if (!grid_barrier(a.bar, a.st)) return;
+    trace_point(a, j, 4);
+
+    // ---------------- phase D (+ A of the next column) ----------------
+    {
+      const int sb = s / TRD_TB;
+      const int ns = ceil_div(m, TRD_TB) - sb;
+      const int qc = symv_qc(ns, nwarps);
+      const int maxQ = (ns + qc - 1) / qc;
+      const int nrb = (m - s + 255) / 256;  // blocks that own rows (and wrote dot partials)
+      const T tauj = (T)h.tau;
+      const bool next = (c + 1 < a.nbp);
+      // the panel's small vectors, staged once per block: V^T v, P^T v and row s of V, P
+      T* sdV = reinterpret_cast<T*>(&dred[1][0]);
+      T* sdP = sdV + TRD_NB;
+      T* sVs = sdP + TRD_NB;
+      T* sPs = sVs + TRD_NB;
+      // each dot product: sum of nrb block partials, 8 lanes per dot product
+      for (int q0 = wid * 4; q0 < 2 * c; q0 += 32) {
+        const int q = q0 + (lane >> 3), l8d = lane & 7;
+        T acc = T(0);
+        if (q < 2 * c) {
+          const int slot = q < c ? q : TRD_NB + (q - c);
+          for (int b = l8d; b < nrb; b += 8) acc += (T)ldcg(a.dotpart + (long)b * 2 * TRD_NB + slot);
+        }
+#pragma unroll
+        for (int o = 4; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (q < 2 * c && l8d == 0) {
+          if (q < c) sdV[q] = acc;
+          else sdP[q - c] = acc;
+        }
+      }
+      for (int t = tid; t < c; t += 256) {
+        sVs[t] = ldcg(VP + s + (long)t * m);
+        sPs[t] = ldcg(VP + s + (long)(TRD_NB + t) * m);
+      }
+      __syncthreads();
+      // p at row s (= j+1): every block needs it for the next column's update
+      T p_s = T(0);
+      if (next) {
+        if (wid == 0) {
+          const int l = s % TRD_TB;
+          T y = T(0);
+          for (int q = lane; q < 1; q += 32) y += ldcg(a.Dpart + ((long)0 * maxQ + q) * TRD_TB + l);
+          for (int R2 = lane; R2 < ns; R2 += 32) y += ldcg(a.Tpart + ((long)0 * ns + R2) * TRD_TB + l);
+          for (int t = lane; t < c; t += 32) y += sVs[t] * sdP[t] - sPs[t] * sdV[t];
+#pragma unroll
+          for (int o = 16; o >= 1; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+          if (lane == 0) dred[0][0] = (double)(tauj * y);
+        }
+        __syncthreads();
+        p_s = (T)dred[0][0];
+      }
+      // rows: 8 lanes per row, groups spread over every block of the grid
+      const int l8 = tid & 7;
+      const int ngroups = gridDim.x * 32;
+      const int sbD = s / TRD_TB;
+      double sq = 0.0;
+      // the loop runs on a warp-uniform base row so every lane reaches the shuffles
+      for (int base = s + blockIdx.x * 32 + wid * 4; base < m; base += ngroups) {
+        const int r = base + (lane >> 3);
+        const bool valid = r < m;
+        const int Rr = r / TRD_TB - sbD, l = r % TRD_TB;
+        const int nq = valid ? Rr / qc + 1 : 0;
+        const int nsv = valid ? ns : 0;
+        T acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = T(0);
+        const T* dp = a.Dpart + (long)Rr * maxQ * TRD_TB + l;
+        for (int q = l8; q < nq; q += 8) acc[0] += ldcg(dp + (long)q * TRD_TB);
+        const T* tp = a.Tpart + (long)Rr * ns * TRD_TB + l;
+        int R2 = Rr + l8;
+        for (; R2 + 56 < nsv; R2 += 64) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) acc[k] += ldcg(tp + (long)(R2 + 8 * k) * TRD_TB);
+        }
+        for (; R2 < nsv; R2 += 8) acc[1] += ldcg(tp + (long)R2 * TRD_TB);
+        T y = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+        const bool upd = next && r >= s + 1;
+        const int j1 = j + 1;
+        T w = T(0);
+        for (int t = l8; valid && t < c; t += 8) {
+          const T vv = ldcg(VP + r + (long)t * m), pp = ldcg(VP + r + (long)(TRD_NB + t) * m);
+          y = fma(vv, sdP[t], y);
+          y = fma(-pp, sdV[t], y);
+          w = fma(vv, sPs[t], w);
+          w = fma(-pp, sVs[t], w);
+        }
+#pragma unroll
+        for (int o = 4; o >= 1; o >>= 1) {
+          y += __shfl_xor_sync(0xffffffffu, y, o);
+          w += __shfl_xor_sync(0xffffffffu, w, o);
+        }
+        if (valid && l8 == 0) {
+          const T vr = (r == s) ? T(1) : ldcg(W + r + (long)j * ldw) * scal;
+          const T p = tauj * y;
+          VP[r + (long)c * m] = vr;
+          VP[r + (long)(TRD_NB + c) * m] = p;
+          PV[r + (long)c * m] = p;
+          PV[r + (long)(TRD_NB + c) * m] = -vr;
+          W[r + (long)j * ldw] = vr;  // the reflector, leading 1 included
+          if (upd) {
+            // column j+1 with all panel terms t <= c; t = c: V[j1, c] = 1, P[j1, c] = p_s
+            w += W[r + (long)j1 * ldw];
+            w = fma(vr, p_s, w);
+            w = fma(-p, T(1), w);
+            W[r + (long)j1 * ldw] = w;
+            if (r >= j1 + 2) sq += (double)w * (double)w;
+          }
+        }
+      }
+      if (next) {
+        sq = block_sum<T>(sq, red8);
+        if (tid == 0) a.normpart[blockIdx.x] = sq;
+      }
+      __syncthreads();  // the staged vectors are rewritten for the next column
+    }
+  }
+}
+
+static unsigned long long* g_trace = nullptr;
+static int g_trace_cols = 0;
+
+template <typename T>
+int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStream_t st, DevStatus* status) {
   TrdWork<T> w = carve<T>(work, m);
-  BSE_CUDA(cudaMemsetAsync(w.norm2, 0, sizeof(double) * (size_t)m, st));
-  BSE_CUDA(cudaMemsetAsync(w.dots, 0, sizeof(double) * (size_t)m * 2 * TRD_NB, st));
+  BSE_CUDA(cudaMemsetAsync(w.bar, 0, 64, st));
+  int dev = 0, nsm = 0, per_sm = 0;
+  BSE_CUDA(cudaGetDevice(&dev));
+  BSE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trd_panel_kernel<T>, 256, 0));
+  if (per_sm < 1) {
+    record_message("tridiagonal panel kernel cannot be resident");
+    return BSE_ERR_CUDA;
+  }
+  per_sm = min(per_sm, 2);
+  if (nsm * per_sm > kMaxGrid) per_sm = max(1, kMaxGrid / nsm);
   const int ncols = m - 1;  // columns 0..m-2 carry a reflector (the last one is trivial)
   for (int j0 = 0; j0 < ncols; j0 += TRD_NB) {
     const int nbp = min(TRD_NB, ncols - j0);
     // zero rows [j0, m) of the panel buffers
     BSE_CUDA(cudaMemset2DAsync(w.VP + j0, (size_t)m * sizeof(T), 0, (size_t)(m - j0) * sizeof(T), 2 * TRD_NB, st));
     BSE_CUDA(cudaMemset2DAsync(w.PV + j0, (size_t)m * sizeof(T), 0, (size_t)(m - j0) * sizeof(T), 2 * TRD_NB, st));
-    for (int c = 0; c < nbp; ++c) {
-      const int j = j0 + c;
-      const int rows = m - j - 1;
-      const int g = ceil_div(rows, 256);
-      {
-        KprofScope ks(K_TRD_COL, st, 0.0, 0.0);
-        trd_colupdate<T><<<g, 256, 0, st>>>(m, j, c, W, ldw, w.VP, w.norm2);
-      }
-      {
-        KprofScope ks(K_TRD_COL, st, 0.0, 0.0);
-        trd_house<T><<<g, 256, 0, st>>>(m, j, c, W, ldw, w.VP, w.PV, w.norm2, w.dots, e, tau);
-      }
-      const int s = j + 1;
-      const int ns = ceil_div(m, TRD_TB) - s / TRD_TB;
-      const int maxQ = ceil_div(ns, TRD_QC);
-      const long items = (long)ns * maxQ;
-      {
-        // algorithmic traffic: the strict lower triangle of the trailing matrix, once
-        const double N = (double)(m - s);
-        KprofScope ks(K_TRD_SYMV, st, N * (N - 1.0) * 0.5 * sizeof(T), 2.0 * N * (N - 1.0));
-        trd_symv<T><<<(unsigned)ceil_div(items, 4), 128, 0, st>>>(m, s, W, ldw, w.VP + (long)c * m, w.Dpart,
-                                                                 w.Tpart, ns, maxQ);
-      }
-      {
-        KprofScope ks(K_TRD_COL, st, 0.0, 0.0);
-        trd_finalize<T><<<g, 256, 0, st>>>(m, j, c, W, ldw, w.VP, w.PV, w.Dpart, w.Tpart, ns, maxQ, w.dots, tau);
-      }
+    // enough blocks for the owned rows and the SYMV items, at most per_sm per SM
+    const int rows = m - j0 - 1;
+    const long sub = (long)ceil_div(rows, TRD_TB);
+    const long want = max((long)ceil_div(rows, 256), (sub * (sub + 1) / 2 + 7) / 8);
+    const int grid = (int)max(1L, min((long)nsm * per_sm, want));
+    PanelArgs<T> pa;
+    pa.m = m; pa.j0 = j0; pa.nbp = nbp; pa.W = W; pa.ldw = ldw; pa.VP = w.VP; pa.PV = w.PV;
+    pa.Dpart = w.Dpart; pa.Tpart = w.Tpart; pa.normpart = w.normpart; pa.dotpart = w.dotpart; pa.e = e; pa.tau = tau;
+    pa.bar = w.bar; pa.st = status;
+    pa.vec = ((ldw * (long)sizeof(T)) % 16 == 0) && ((reinterpret_cast<uintptr_t>(W) % 16) == 0);
+    pa.trace = g_trace;
+    pa.trace_cols = g_trace_cols;
+    if (grid * 256 < rows + 1 && grid < nsm * per_sm) {
+      record_message("tridiagonal panel grid too small");
+      return BSE_ERR_CUDA;
     }
-    BSE_LAUNCH_CHECK();
+    {
+      // charged: the strict lower triangles of the nbp trailing matrices, once each
+      double bytes = 0.0, flops = 0.0;
+      for (int c = 0; c < nbp; ++c) {
+        const double N = (double)(m - j0 - c - 1);
+        bytes += N * (N - 1.0) * 0.5 * sizeof(T);
+        flops += 2.0 * N * (N - 1.0);
+      }
+      KprofScope ks(K_TRD_SYMV, st, bytes, flops);
+      void* args[] = {&pa};
+      BSE_CUDA(cudaLaunchCooperativeKernel((const void*)trd_panel_kernel<T>, dim3(grid), dim3(256), args, 0, st));
+    }
     const int s2 = j0 + nbp;
     const int N = m - s2;
     if (N > 1 && s2 < ncols) {
@@ -308,19 +644,35 @@ int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStr
 
 template size_t trd_worksize<double>(int);
 template size_t trd_worksize<float>(int);
-template int tridiagonalize<double>(int, double*, long, double*, double*, void*, cudaStream_t);
-template int tridiagonalize<float>(int, float*, long, double*, float*, void*, cudaStream_t);
+template int tridiagonalize<double>(int, double*, long, double*, double*, void*, cudaStream_t, DevStatus*);
+template int tridiagonalize<float>(int, float*, long, double*, float*, void*, cudaStream_t, DevStatus*);
 
 }  // namespace bse
+
+extern "C" int bse_debug_trace_tridiag(void* dev_buffer, int columns) {
+  bse::g_trace = reinterpret_cast<unsigned long long*>(dev_buffer);
+  bse::g_trace_cols = dev_buffer ? columns : 0;
+  return BSE_OK;
+}
+
+extern "C" int bse_stage_tridiag_grid(int m, int fp32) {
+  int dev = 0, nsm = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (fp32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bse::trd_panel_kernel<float>, 256, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bse::trd_panel_kernel<double>, 256, 0);
+  return nsm * (per < 2 ? per : 2);
+}
 
 extern "C" size_t bse_stage_tridiag_worksize(int m, int fp32) {
   return fp32 ? bse::trd_worksize<float>(m) : bse::trd_worksize<double>(m);
 }
 
 extern "C" int bse_stage_tridiag(int m, void* W, int ldw, double* e, void* tau, int fp32, void* work,
-                                 void* stream) {
-  if (m < 2 || !W || ldw < m || !e || !tau || !work) return BSE_ERR_ARG;
+                                 int* dev_status, void* stream) {
+  if (m < 2 || !W || ldw < m || !e || !tau || !work || !dev_status) return BSE_ERR_ARG;
+  auto* st = reinterpret_cast<bse::DevStatus*>(dev_status);
   if (fp32)
-    return bse::tridiagonalize<float>(m, (float*)W, ldw, e, (float*)tau, work, (cudaStream_t)stream);
-  return bse::tridiagonalize<double>(m, (double*)W, ldw, e, (double*)tau, work, (cudaStream_t)stream);
+    return bse::tridiagonalize<float>(m, (float*)W, ldw, e, (float*)tau, work, (cudaStream_t)stream, st);
+  return bse::tridiagonalize<double>(m, (double*)W, ldw, e, (double*)tau, work, (cudaStream_t)stream, st);
 }

@@ -42,6 +42,10 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// W's leading dimension, padded to 32 elements so 16-byte vector loads of its
+// columns stay aligned whatever n is.
+size_t w_ld(int n) { return ((2 * (size_t)n + 31) / 32) * 32; }
+
 size_t workspace_bytes(int n, int precision) {
   const size_t m = 2 * (size_t)n;
   const bool f32 = precision != BSE_FP64;
@@ -50,7 +54,7 @@ size_t workspace_bytes(int n, int precision) {
   b += 2 * al256(16 * (size_t)n * n);         // A, B staging
   b += al256(8 * m * m);                       // M (FP64)
   if (f32) b += al256(4 * m * m);              // L (FP32)
-  b += al256(ts * m * m);                      // W
+  b += al256(ts * w_ld(n) * m);                // W (leading dimension padded)
   b += al256(8 * m) + al256(ts * m) + al256(8 * (size_t)n);  // e, tau, lambda
   b += al256(8 * m * n);                       // Vs
   b += 2 * al256(16 * m * n);                  // X, Y
@@ -88,7 +92,8 @@ int Workspace::init(int n_, int precision_) {
   B = (double*)take(16 * (size_t)n * n);
   M = (double*)take(8 * m * m);
   Lf = f32 ? (float*)take(4 * m * m) : nullptr;
-  W = take(ts * m * m);
+  ldw = (int)w_ld(n);
+  W = take(ts * (size_t)ldw * m);
   e = (double*)take(8 * m);
   tau = take(ts * m);
   lam = (double*)take(8 * (size_t)n);
@@ -249,13 +254,13 @@ int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, co
     double* tau = (double*)ws->tau;
     BSE_TRY(potrf<double>(m, ws->M, m, ws->scratch, ws->status, s));
     if (tm) cudaEventRecord(ev[2], s);
-    BSE_TRY(form_W<double>(n, ws->M, m, W, m, s));
+    BSE_TRY(form_W<double>(n, ws->M, m, W, ws->ldw, s));
     if (tm) cudaEventRecord(ev[3], s);
-    BSE_TRY(tridiagonalize<double>(m, W, m, ws->e, tau, ws->scratch, s));
+    BSE_TRY(tridiagonalize<double>(m, W, ws->ldw, ws->e, tau, ws->scratch, s, ws->status));
     if (tm) cudaEventRecord(ev[4], s);
     BSE_TRY(tdeig(m, ws->e, ws->lam, ws->Vs, (double*)ws->scratch, ws->status, s));
     if (tm) cudaEventRecord(ev[5], s);
-    BSE_TRY(backtransform<double>(m, ws->M, m, W, m, tau, ws->Vs, ws->lam, ws->X, want_Y ? ws->Y : nullptr, m,
+    BSE_TRY(backtransform<double>(m, ws->M, m, W, ws->ldw, tau, ws->Vs, ws->lam, ws->X, want_Y ? ws->Y : nullptr, m,
                                   ws->scratch, s));
     if (tm) cudaEventRecord(ev[6], s);
   } else {
@@ -263,14 +268,14 @@ int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, co
     float* tau = (float*)ws->tau;
     BSE_TRY(potrf<float>(m, ws->Lf, m, ws->scratch, ws->status, s));
     if (tm) cudaEventRecord(ev[2], s);
-    BSE_TRY(form_W<float>(n, ws->Lf, m, W, m, s));
+    BSE_TRY(form_W<float>(n, ws->Lf, m, W, ws->ldw, s));
     if (tm) cudaEventRecord(ev[3], s);
-    BSE_TRY(tridiagonalize<float>(m, W, m, ws->e, tau, ws->scratch, s));
+    BSE_TRY(tridiagonalize<float>(m, W, ws->ldw, ws->e, tau, ws->scratch, s, ws->status));
     if (tm) cudaEventRecord(ev[4], s);
     BSE_TRY(tdeig(m, ws->e, ws->lam, ws->Vs, (double*)ws->scratch, ws->status, s));
     if (tm) cudaEventRecord(ev[5], s);
     const bool refine_now = precision == BSE_MIXED_REFINED;
-    BSE_TRY(backtransform<float>(m, ws->Lf, m, W, m, tau, ws->Vs, ws->lam, ws->X,
+    BSE_TRY(backtransform<float>(m, ws->Lf, m, W, ws->ldw, tau, ws->Vs, ws->lam, ws->X,
                                  (want_Y && !refine_now) ? ws->Y : nullptr, m, ws->scratch, s));
     if (tm) cudaEventRecord(ev[6], s);
     if (refine_now) {

@@ -17,6 +17,7 @@ struct Workspace {
   double* M = nullptr;                // FP64 M (L and then Phi on the FP64 path)
   float* Lf = nullptr;                // FP32 copy of M -> L -> Phi (mixed paths)
   void* W = nullptr;                  // W, then the reflectors (FP64 or FP32)
+  int ldw = 0;                        // W's leading dimension (2n padded to 32)
   double* e = nullptr;                // sub-diagonal of T
   void* tau = nullptr;
   double* lam = nullptr;

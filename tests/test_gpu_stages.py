@@ -114,7 +114,7 @@ def _W_input(n, seed):
     return alg1.step3_W(alg1.step2_cholesky(alg1.step1_M(p.A, p.B)))
 
 
-@pytest.mark.parametrize("n", [1, 3, 33, 70, 100])
+@pytest.mark.parametrize("n", [1, 3, 33, 70, 100, 129, 257])
 @pytest.mark.parametrize("fp32", [0, 1])
 def test_tridiag(n, fp32):
     """Blocked skew reduction reproduces the unblocked literal H A H reduction (same
@@ -128,9 +128,11 @@ def test_tridiag(n, fp32):
     e = torch.empty(m, dtype=torch.float64, device="cuda")
     tau = torch.empty(m, dtype=torch.float32 if fp32 else torch.float64, device="cuda")
     work = torch.empty(L.bse_stage_tridiag_worksize(m, fp32), dtype=torch.uint8, device="cuda")
-    bse.check(L.bse_stage_tridiag(m, Wd.data_ptr(), m, e.data_ptr(), tau.data_ptr(), fp32, work.data_ptr(), None),
-              "tridiag")
+    st = _status(torch)
+    bse.check(L.bse_stage_tridiag(m, Wd.data_ptr(), m, e.data_ptr(), tau.data_ptr(), fp32, work.data_ptr(),
+                                  st.data_ptr(), None), "tridiag")
     torch.cuda.synchronize()
+    assert st.cpu().numpy()[0] == 0
     ref = alg1.alg3_step1_tridiagonalize(W)
     eg = e.cpu().numpy()[: m - 1]
     scale = np.max(np.abs(W))

@@ -21,9 +21,12 @@
 // Pairs closer than the current error level are not divided by their gap
 // (E11_ij = 0); the next sweep sees them again.
 #include <float.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <utility>
+#include <vector>
 
 #include "common.cuh"
 #include "gemm_simt.cuh"
@@ -35,15 +38,20 @@ namespace bse {
 static inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct RefWork {
-  double *Ur, *Ui, *Pr, *Pi, *Vr, *Vi;
-  double *G1, *G2, *G3, *G4, *Fa, *Fb, *Fc, *Fd;
+  double *Ur, *Ui, *Pr, *Pi;          // FP64 U = Q^H X and P = M U (then R)
+  float *Urf, *Uif, *Rrf, *Rif;       // FP32 copies for the projections
+  float *dUr, *dUi;                   // FP32 correction U E11 + conj(U) E21
+  float *G1, *G2, *G3, *G4, *Fa, *Fb, *Fc, *Fd;
   double *lam_new, *bnorm, *scal;
   unsigned long long* maxes;  // [0] max resid, [1] max dlam (as ordered bit patterns)
+  int* cid;                   // cluster id per column
+  int2* clus;                 // (first column, size) per cluster
 };
 
 size_t refine_worksize(int n) {
   const size_t m = 2 * (size_t)n;
-  return 6 * al256(8 * m * n) + 8 * al256(8 * (size_t)n * n) + 2 * al256(8 * (size_t)n) + al256(64) + al256(64);
+  return 4 * al256(8 * m * n) + 6 * al256(4 * m * n) + 8 * al256(4 * (size_t)n * n) + 2 * al256(8 * (size_t)n) +
+         al256(64) + al256(64) + al256(4 * (size_t)n) + al256(8 * ((size_t)n / 2 + 2));
 }
 
 static RefWork carve_ref(void* work, int n) {
@@ -57,15 +65,19 @@ static RefWork carve_ref(void* work, int n) {
   };
   w.Ur = (double*)take(8 * m * n); w.Ui = (double*)take(8 * m * n);
   w.Pr = (double*)take(8 * m * n); w.Pi = (double*)take(8 * m * n);
-  w.Vr = (double*)take(8 * m * n); w.Vi = (double*)take(8 * m * n);
-  w.G1 = (double*)take(8 * (size_t)n * n); w.G2 = (double*)take(8 * (size_t)n * n);
-  w.G3 = (double*)take(8 * (size_t)n * n); w.G4 = (double*)take(8 * (size_t)n * n);
-  w.Fa = (double*)take(8 * (size_t)n * n); w.Fb = (double*)take(8 * (size_t)n * n);
-  w.Fc = (double*)take(8 * (size_t)n * n); w.Fd = (double*)take(8 * (size_t)n * n);
+  w.Urf = (float*)take(4 * m * n); w.Uif = (float*)take(4 * m * n);
+  w.Rrf = (float*)take(4 * m * n); w.Rif = (float*)take(4 * m * n);
+  w.dUr = (float*)take(4 * m * n); w.dUi = (float*)take(4 * m * n);
+  w.G1 = (float*)take(4 * (size_t)n * n); w.G2 = (float*)take(4 * (size_t)n * n);
+  w.G3 = (float*)take(4 * (size_t)n * n); w.G4 = (float*)take(4 * (size_t)n * n);
+  w.Fa = (float*)take(4 * (size_t)n * n); w.Fb = (float*)take(4 * (size_t)n * n);
+  w.Fc = (float*)take(4 * (size_t)n * n); w.Fd = (float*)take(4 * (size_t)n * n);
   w.lam_new = (double*)take(8 * (size_t)n);
   w.bnorm = (double*)take(8 * (size_t)n);
   w.scal = (double*)take(64);
   w.maxes = (unsigned long long*)take(64);
+  w.cid = (int*)take(4 * (size_t)n);
+  w.clus = (int2*)take(8 * ((size_t)n / 2 + 2));
   return w;
 }
 
@@ -124,9 +136,12 @@ __device__ __forceinline__ double block_sum256(double v, double* red) {
   return t;
 }
 
-// Per column: Rayleigh quotient, normalisation, residual R = P - K U lambda (in place in P).
+// Per column: Rayleigh quotient, normalisation, residual R = P - K U lambda (FP32 copy
+// for the projections; its norm in FP64 for the convergence test).
 __global__ void __launch_bounds__(256) ref_colstats(int n, const double* __restrict__ Ur, const double* __restrict__ Ui,
-                                                    double* __restrict__ Pr, double* __restrict__ Pi,
+                                                    const double* __restrict__ Pr, const double* __restrict__ Pi,
+                                                    float* __restrict__ Urf, float* __restrict__ Uif,
+                                                    float* __restrict__ Rrf, float* __restrict__ Rif,
                                                     const double* __restrict__ lam_old, double* __restrict__ lam_new,
                                                     double* __restrict__ bnorm, const double* __restrict__ scal,
                                                     unsigned long long* __restrict__ maxes) {
@@ -149,9 +164,11 @@ __global__ void __launch_bounds__(256) ref_colstats(int n, const double* __restr
     double kr, ki;  // (K u)_i
     if (i < n) { kr = Ui[n + i + c]; ki = -Ur[n + i + c]; }
     else { kr = -Ui[i - n + c]; ki = Ur[i - n + c]; }
-    const double r1 = Pr[i + c] - lam * kr, r2 = Pi[i + c] - lam * ki;
-    Pr[i + c] = r1;
-    Pi[i + c] = r2;
+    const double r1 = Pr[i + c] - lam * kr, r2 = Pi[i + c] - lam * ki;  // P stays intact
+    Rrf[i + c] = (float)r1;
+    Rif[i + c] = (float)r2;
+    Urf[i + c] = (float)Ur[i + c];
+    Uif[i + c] = (float)Ui[i + c];
     rr += r1 * r1 + r2 * r2;
   }
   rr = block_sum256(rr, red);
@@ -166,11 +183,12 @@ __global__ void __launch_bounds__(256) ref_colstats(int n, const double* __restr
 }
 
 // E from C1 = U^H R, C2 = U^T R (given as G1 = Ur^T Rr, G2 = Ui^T Ri, G3 = Ur^T Ri, G4 = Ui^T Rr).
-__global__ void ref_buildE(int n, const double* __restrict__ G1, const double* __restrict__ G2,
-                           const double* __restrict__ G3, const double* __restrict__ G4,
-                           const double* __restrict__ lam, const double* __restrict__ bnorm, double gap_tol,
-                           double* __restrict__ Fa, double* __restrict__ Fb, double* __restrict__ Fc,
-                           double* __restrict__ Fd) {
+__global__ void ref_buildE(int n, const float* __restrict__ G1, const float* __restrict__ G2,
+                           const float* __restrict__ G3, const float* __restrict__ G4,
+                           const double* __restrict__ lam, const double* __restrict__ bnorm,
+                           const int* __restrict__ cluster_id,
+                           float* __restrict__ Fa, float* __restrict__ Fb, float* __restrict__ Fc,
+                           float* __restrict__ Fd) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
   if (i >= n) return;
   const long k = i + (long)j * n;
@@ -183,17 +201,282 @@ __global__ void ref_buildE(int n, const double* __restrict__ G1, const double* _
     e1r = 0.5 * (1.0 - bnorm[j]);
   } else {
     const double d = lj - li;
-    if (fabs(d) > gap_tol * fmax(fabs(li), fabs(lj))) {
+    // pairs inside one cluster were resolved exactly by its Rayleigh-Ritz step
+    if (cluster_id[i] != cluster_id[j] && fabs(d) > 1e-14 * fmax(fabs(li), fabs(lj))) {
       e1r = c1r / d;
       e1i = c1i / d;
     }
   }
   const double s = -1.0 / (li + lj);
   const double e2r = c2r * s, e2i = c2i * s;
-  Fa[k] = e1r + e2r;
-  Fb[k] = e2i - e1i;
-  Fc[k] = e1i + e2i;
-  Fd[k] = e1r - e2r;
+  Fa[k] = (float)(e1r + e2r);
+  Fb[k] = (float)(e2i - e1i);
+  Fc[k] = (float)(e1i + e2i);
+  Fd[k] = (float)(e1r - e2r);
+}
+
+// U += dU (FP64 += FP32 correction)
+__global__ void ref_apply(long count, double* __restrict__ Ur, double* __restrict__ Ui, const float* __restrict__ dUr,
+                          const float* __restrict__ dUi) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+    Ur[i] += (double)dUr[i];
+    Ui[i] += (double)dUi[i];
+  }
+}
+
+// ---- cluster Rayleigh-Ritz ---------------------------------------------------
+// For a run I of k <= kRRMax consecutive eigenvalues closer than the current
+// error level, the first-order correction cannot separate the pair mixing, so
+// the pencil is solved exactly on span(U_I) in FP64:
+//   A_I = U_I^H M U_I = U_I^H P_I,  B_I = U_I^H K U_I,  A_I c = mu B_I c,
+// with B_I = L L^H, C = L^{-1} A_I L^{-H} diagonalised by cyclic complex Jacobi,
+// and U_I <- U_I Cc, P_I <- P_I Cc (P is linear in U), Cc = L^{-H} Z, so that
+// Cc^H B_I Cc = I (the Theorem 3 normalisation) and the mu come out ascending.
+constexpr int kRRMax = 32;
+
+struct cplx {
+  double x, y;
+};
+__device__ __forceinline__ cplx cmk(double a, double b) { return {a, b}; }
+__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ cplx csub(cplx a, cplx b) { return {a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ cplx cconjmul(cplx a, cplx b) { return {a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x}; }
+__device__ __forceinline__ cplx cconj(cplx a) { return {a.x, -a.y}; }
+__device__ __forceinline__ cplx cscale(cplx a, double s) { return {a.x * s, a.y * s}; }
+
+__global__ void __launch_bounds__(256) ref_cluster_rr(int n, const int2* __restrict__ clusters, double* Ur, double* Ui,
+                                                      double* Pr, double* Pi, double* lam_out) {
+  __shared__ cplx A[kRRMax][kRRMax + 1];
+  __shared__ cplx Bm[kRRMax][kRRMax + 1];
+  __shared__ cplx Z[kRRMax][kRRMax + 1];
+  __shared__ double mu[kRRMax];
+  __shared__ int order[kRRMax];
+  __shared__ double rot[4];
+  __shared__ double off;
+  const int2 cl = clusters[blockIdx.x];
+  const int c0 = cl.x, k = cl.y;
+  const int tid = threadIdx.x;
+  const long m = 2L * n;
+  // 1. A = U^H P and B = U^H K U over the cluster's columns, FP64, thread per (a, b)
+  for (int pr = tid; pr < k * k; pr += blockDim.x) {
+    const int a = pr % k, b = pr / k;
+    const double* ura = Ur + (long)(c0 + a) * m;
+    const double* uia = Ui + (long)(c0 + a) * m;
+    const double* urb = Ur + (long)(c0 + b) * m;
+    const double* uib = Ui + (long)(c0 + b) * m;
+    const double* prb = Pr + (long)(c0 + b) * m;
+    const double* pib = Pi + (long)(c0 + b) * m;
+    cplx sa = cmk(0, 0), sb = cmk(0, 0);
+    for (int i = 0; i < n; ++i) {
+      const cplx ut = cmk(ura[i], uia[i]), ub = cmk(ura[n + i], uia[n + i]);
+      sa = cadd(sa, cconjmul(ut, cmk(prb[i], pib[i])));
+      sa = cadd(sa, cconjmul(ub, cmk(prb[n + i], pib[n + i])));
+      // (K u)_top = -i u_bot = (Ui_bot, -Ur_bot); (K u)_bot = i u_top = (-Ui_top, Ur_top)
+      sb = cadd(sb, cconjmul(ut, cmk(uib[n + i], -urb[n + i])));
+      sb = cadd(sb, cconjmul(ub, cmk(-uib[i], urb[i])));
+    }
+    A[a][b] = sa;
+    Bm[a][b] = sb;
+  }
+  __syncthreads();
+  // exact Hermitian pencils from the lower halves
+  for (int pr = tid; pr < k * k; pr += blockDim.x) {
+    const int a = pr % k, b = pr / k;
+    if (a > b) {
+      const cplx x = cscale(cadd(A[a][b], cconj(A[b][a])), 0.5);
+      const cplx y = cscale(cadd(Bm[a][b], cconj(Bm[b][a])), 0.5);
+      A[a][b] = x;
+      Bm[a][b] = y;
+    }
+  }
+  __syncthreads();
+  for (int pr = tid; pr < k * k; pr += blockDim.x) {
+    const int a = pr % k, b = pr / k;
+    if (a < b) {
+      A[a][b] = cconj(A[b][a]);
+      Bm[a][b] = cconj(Bm[b][a]);
+    } else if (a == b) {
+      A[a][a].y = 0.0;
+      Bm[a][a].y = 0.0;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // B = L L^H, L (lower) in Bm
+    for (int j = 0; j < k; ++j) {
+      double d = Bm[j][j].x;
+      for (int t = 0; t < j; ++t) d -= Bm[j][t].x * Bm[j][t].x + Bm[j][t].y * Bm[j][t].y;
+      d = sqrt(fmax(d, 1e-300));
+      Bm[j][j] = cmk(d, 0.0);
+      for (int i = j + 1; i < k; ++i) {
+        cplx s2 = Bm[i][j];
+        for (int t = 0; t < j; ++t) s2 = csub(s2, cmul(Bm[i][t], cconj(Bm[j][t])));
+        Bm[i][j] = cscale(s2, 1.0 / d);
+      }
+    }
+  }
+  __syncthreads();
+  // X = L^{-1} A, one column per thread, into Z
+  if (tid < k) {
+    const int col = tid;
+    for (int i = 0; i < k; ++i) {
+      cplx s2 = A[i][col];
+      for (int t = 0; t < i; ++t) s2 = csub(s2, cmul(Bm[i][t], Z[t][col]));
+      Z[i][col] = cscale(s2, 1.0 / Bm[i][i].x);
+    }
+  }
+  __syncthreads();
+  // C = X L^{-H}: row r of C solves L conj(C[r,:])^T = conj(X[r,:])^T; y = conj(C[r,:]) into A
+  if (tid < k) {
+    const int row = tid;
+    for (int i = 0; i < k; ++i) {
+      cplx s2 = cconj(Z[row][i]);
+      for (int t = 0; t < i; ++t) s2 = csub(s2, cmul(Bm[i][t], A[row][t]));
+      A[row][i] = cscale(s2, 1.0 / Bm[i][i].x);
+    }
+  }
+  __syncthreads();
+  for (int pr = tid; pr < k * k; pr += blockDim.x) {
+    const int a = pr % k, b = pr / k;
+    A[a][b] = cconj(A[a][b]);  // C[a][b]
+  }
+  __syncthreads();
+  for (int pr = tid; pr < k * k; pr += blockDim.x) {
+    const int a = pr % k, b = pr / k;
+    if (a < b) A[a][b] = cconj(A[b][a]);
+    if (a == b) A[a][a].y = 0.0;
+    Z[a][b] = cmk(a == b ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  // cyclic Jacobi on the Hermitian C (in A), eigenvectors in Z
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    if (tid == 0) {
+      double o = 0.0, dg = 0.0;
+      for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b) {
+          const double v = A[a][b].x * A[a][b].x + A[a][b].y * A[a][b].y;
+          if (a == b) dg += v;
+          else o += v;
+        }
+      off = (o <= 1e-30 * dg) ? -1.0 : o;
+    }
+    __syncthreads();
+    if (off < 0.0) break;
+    for (int p = 0; p < k - 1; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        if (tid == 0) {
+          const cplx apq = A[p][q];
+          const double r = sqrt(apq.x * apq.x + apq.y * apq.y);
+          if (r < 1e-300) {
+            rot[0] = 1.0; rot[1] = 0.0; rot[2] = 1.0; rot[3] = 0.0;
+          } else {
+            const double theta = (A[q][q].x - A[p][p].x) / (2.0 * r);
+            const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            const double c = 1.0 / sqrt(t * t + 1.0);
+            rot[0] = c; rot[1] = t * c; rot[2] = apq.x / r; rot[3] = apq.y / r;  // e^{i phi}
+          }
+        }
+        __syncthreads();
+        const double c = rot[0], sn = rot[1];
+        const cplx ph = cmk(rot[2], rot[3]);
+        // similarity by G = diag(1, e^{-i phi}) * [[c, s], [-s, c]] on (p, q): columns ...
+        if (tid < k) {
+          const int r2 = tid;
+          const cplx ap = A[r2][p], aq = cmul(A[r2][q], cconj(ph));
+          A[r2][p] = csub(cscale(ap, c), cscale(aq, sn));
+          A[r2][q] = cadd(cscale(ap, sn), cscale(aq, c));
+          const cplx zp = Z[r2][p], zq = cmul(Z[r2][q], cconj(ph));
+          Z[r2][p] = csub(cscale(zp, c), cscale(zq, sn));
+          Z[r2][q] = cadd(cscale(zp, sn), cscale(zq, c));
+        }
+        __syncthreads();
+        // ... and rows (G^H on the left)
+        if (tid < k) {
+          const int c2 = tid;
+          const cplx ap = A[p][c2], aq = cmul(A[q][c2], ph);
+          A[p][c2] = csub(cscale(ap, c), cscale(aq, sn));
+          A[q][c2] = cadd(cscale(ap, sn), cscale(aq, c));
+        }
+        __syncthreads();
+      }
+  }
+  if (tid == 0) {
+    for (int a = 0; a < k; ++a) {
+      mu[a] = A[a][a].x;
+      order[a] = a;
+    }
+    for (int a = 0; a < k; ++a)
+      for (int b = a + 1; b < k; ++b)
+        if (mu[order[b]] < mu[order[a]]) {
+          const int t = order[a]; order[a] = order[b]; order[b] = t;
+        }
+  }
+  __syncthreads();
+  // Cc = L^{-H} Z in ascending order, one column per thread, into Bm's upper part? -> into A
+  if (tid < k) {
+    const int col = order[tid];
+    for (int i = k - 1; i >= 0; --i) {
+      cplx s2 = Z[i][col];
+      for (int t = i + 1; t < k; ++t) s2 = csub(s2, cmul(cconj(Bm[t][i]), A[t][tid]));
+      A[i][tid] = cscale(s2, 1.0 / Bm[i][i].x);
+    }
+  }
+  __syncthreads();
+  if (tid < k) lam_out[c0 + tid] = mu[order[tid]];
+  // U_I <- U_I Cc, P_I <- P_I Cc, one row per thread
+  for (long i = tid; i < m; i += blockDim.x) {
+    cplx u[kRRMax], pp[kRRMax];
+    for (int a = 0; a < k; ++a) {
+      u[a] = cmk(Ur[i + (long)(c0 + a) * m], Ui[i + (long)(c0 + a) * m]);
+      pp[a] = cmk(Pr[i + (long)(c0 + a) * m], Pi[i + (long)(c0 + a) * m]);
+    }
+    for (int b = 0; b < k; ++b) {
+      cplx su = cmk(0, 0), sp = cmk(0, 0);
+      for (int a = 0; a < k; ++a) {
+        su = cadd(su, cmul(u[a], A[a][b]));
+        sp = cadd(sp, cmul(pp[a], A[a][b]));
+      }
+      Ur[i + (long)(c0 + b) * m] = su.x;
+      Ui[i + (long)(c0 + b) * m] = su.y;
+      Pr[i + (long)(c0 + b) * m] = sp.x;
+      Pi[i + (long)(c0 + b) * m] = sp.y;
+    }
+  }
+}
+
+// Runs of consecutive eigenvalues with relative gaps below tau, split to at most
+// kRRMax at their widest internal gap; cluster_id[j] = first index of j's run.
+static void find_clusters(const std::vector<double>& lam, double tau, std::vector<int2>& out, std::vector<int>& id) {
+  const int n = (int)lam.size();
+  out.clear();
+  id.resize(n);
+  int a = 0;
+  while (a < n) {
+    int b = a + 1;
+    while (b < n && (lam[b] - lam[b - 1]) <= tau * fabs(lam[b])) ++b;
+    std::vector<std::pair<int, int>> stack{{a, b}};
+    while (!stack.empty()) {
+      const std::pair<int, int> xy = stack.back();
+      stack.pop_back();
+      const int x = xy.first, y = xy.second;
+      if (y - x <= kRRMax) {
+        for (int j = x; j < y; ++j) id[j] = x;
+        if (y - x >= 2) out.push_back(make_int2(x, y - x));
+        continue;
+      }
+      int cut = x + 1;
+      double best = -1.0;
+      for (int j = x + 1; j < y; ++j)
+        if (lam[j] - lam[j - 1] > best) {
+          best = lam[j] - lam[j - 1];
+          cut = j;
+        }
+      stack.push_back({x, cut});
+      stack.push_back({cut, y});
+    }
+    a = b;
+  }
 }
 
 int refine(int n, const double* M, double* lam, double* X, int max_sweeps, double tol, void* work, DevStatus* st,
@@ -215,8 +498,12 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
   const double fro = sqrt(fro2);
   BSE_CUDA(cudaMemcpyAsync(w.scal, &fro, 8, cudaMemcpyHostToDevice, s));
   const double res_target = tol > 0 ? tol : 4.0 * (double)n * DBL_EPSILON;
+  static const bool verbose = getenv("BSE_REFINE_VERBOSE") != nullptr;
   int sweeps = 0;
-  double res = 0, dl = 0;
+  double res = 0, dl = 0, dl_level = 0;
+  std::vector<double> hlam(n);
+  std::vector<int2> clusters;
+  std::vector<int> cid;
   *dlam_first = 0;
   for (int it = 0;; ++it) {
     // P = M U
@@ -224,7 +511,8 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     BSE_TRY(gemm<double>(m, n, m, 1.0, M, m, false, w.Ui, m, false, 0.0, w.Pi, m, s));
     BSE_CUDA(cudaMemsetAsync(w.maxes, 0, 16, s));
     kcount(1);
-    ref_colstats<<<n, 256, 0, s>>>(n, w.Ur, w.Ui, w.Pr, w.Pi, lam, w.lam_new, w.bnorm, w.scal, w.maxes);
+    ref_colstats<<<n, 256, 0, s>>>(n, w.Ur, w.Ui, w.Pr, w.Pi, w.Urf, w.Uif, w.Rrf, w.Rif, lam, w.lam_new, w.bnorm,
+                                   w.scal, w.maxes);
     BSE_LAUNCH_CHECK();
     unsigned long long hm[2];
     BSE_CUDA(cudaMemcpyAsync(hm, w.maxes, 16, cudaMemcpyDeviceToHost, s));
@@ -233,26 +521,50 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     memcpy(&res, &hm[0], 8);
     memcpy(&dl, &hm[1], 8);
     if (it == 0) *dlam_first = dl;
-    const bool converged = (res <= res_target && (it > 0 && dl <= 1e-13));
+    if (it == 0) dl_level = dl;
+    if (verbose) fprintf(stderr, "[bse refine] n=%d sweep %d: max scaled residual %.3e, max rel dlambda %.3e\n", n, it, res, dl);
+    // the Rayleigh quotient's error is second order in the vectors' error, so once
+    // a sweep moves the eigenvalues by <= 1e-12 (relative) they are settled
+    const bool converged = (res <= res_target && (it > 0 && dl <= 1e-12));
     if (converged || it >= max_sweeps) break;
-    // C1, C2 from four real products
-    BSE_TRY(gemm<double>(n, n, m, 1.0, w.Ur, m, true, w.Pr, m, false, 0.0, w.G1, n, s));
-    BSE_TRY(gemm<double>(n, n, m, 1.0, w.Ui, m, true, w.Pi, m, false, 0.0, w.G2, n, s));
-    BSE_TRY(gemm<double>(n, n, m, 1.0, w.Ur, m, true, w.Pi, m, false, 0.0, w.G3, n, s));
-    BSE_TRY(gemm<double>(n, n, m, 1.0, w.Ui, m, true, w.Pr, m, false, 0.0, w.G4, n, s));
-    const double gap_tol = fmax(1e-14, 4.0 * dl);
+    // clusters: runs closer than ~20x the current eigenvalue error level
+    BSE_CUDA(cudaMemcpyAsync(hlam.data(), lam, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    BSE_CUDA(cudaStreamSynchronize(s));
+    const double tau = fmin(1e-3, fmax(1e-13, 20.0 * (it == 0 ? dl_level : dl)));
+    find_clusters(hlam, tau, clusters, cid);
+    BSE_CUDA(cudaMemcpyAsync(w.cid, cid.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+    if (!clusters.empty()) {
+      BSE_CUDA(cudaMemcpyAsync(w.clus, clusters.data(), sizeof(int2) * clusters.size(), cudaMemcpyHostToDevice, s));
+      kcount(2);
+      ref_cluster_rr<<<(unsigned)clusters.size(), 256, 0, s>>>(n, w.clus, w.Ur, w.Ui, w.Pr, w.Pi, lam);
+      BSE_LAUNCH_CHECK();
+      // statistics and FP32 copies again for the rotated columns
+      BSE_CUDA(cudaMemsetAsync(w.maxes, 0, 16, s));
+      ref_colstats<<<n, 256, 0, s>>>(n, w.Ur, w.Ui, w.Pr, w.Pi, w.Urf, w.Uif, w.Rrf, w.Rif, lam, w.lam_new, w.bnorm,
+                                     w.scal, w.maxes);
+      BSE_LAUNCH_CHECK();
+      BSE_CUDA(cudaMemcpyAsync(lam, w.lam_new, 8 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    }
+    // the host vectors must outlive the asynchronous uploads above
+    BSE_CUDA(cudaStreamSynchronize(s));
+    if (verbose) fprintf(stderr, "[bse refine] n=%d sweep %d: %zu clusters (tau %.1e)\n", n, it, clusters.size(), tau);
+    // C1 = U^H R, C2 = U^T R from four real FP32 products (R is residual-sized, so FP32
+    // rounding of these products is eps32 relative to a quantity that is itself small)
+    BSE_TRY(gemm<float>(n, n, m, 1.0, w.Urf, m, true, w.Rrf, m, false, 0.0, w.G1, n, s));
+    BSE_TRY(gemm<float>(n, n, m, 1.0, w.Uif, m, true, w.Rif, m, false, 0.0, w.G2, n, s));
+    BSE_TRY(gemm<float>(n, n, m, 1.0, w.Urf, m, true, w.Rif, m, false, 0.0, w.G3, n, s));
+    BSE_TRY(gemm<float>(n, n, m, 1.0, w.Uif, m, true, w.Rrf, m, false, 0.0, w.G4, n, s));
     kcount(1);
-    ref_buildE<<<eg, 128, 0, s>>>(n, w.G1, w.G2, w.G3, w.G4, lam, w.bnorm, gap_tol, w.Fa, w.Fb, w.Fc, w.Fd);
+    ref_buildE<<<eg, 128, 0, s>>>(n, w.G1, w.G2, w.G3, w.G4, lam, w.bnorm, w.cid, w.Fa, w.Fb, w.Fc, w.Fd);
     BSE_LAUNCH_CHECK();
-    // V = U + Ur [Fa Fc] + Ui [Fb Fd]
-    BSE_CUDA(cudaMemcpyAsync(w.Vr, w.Ur, 8 * (size_t)m * n, cudaMemcpyDeviceToDevice, s));
-    BSE_CUDA(cudaMemcpyAsync(w.Vi, w.Ui, 8 * (size_t)m * n, cudaMemcpyDeviceToDevice, s));
-    BSE_TRY(gemm<double>(m, n, n, 1.0, w.Ur, m, false, w.Fa, n, false, 1.0, w.Vr, m, s));
-    BSE_TRY(gemm<double>(m, n, n, 1.0, w.Ui, m, false, w.Fb, n, false, 1.0, w.Vr, m, s));
-    BSE_TRY(gemm<double>(m, n, n, 1.0, w.Ur, m, false, w.Fc, n, false, 1.0, w.Vi, m, s));
-    BSE_TRY(gemm<double>(m, n, n, 1.0, w.Ui, m, false, w.Fd, n, false, 1.0, w.Vi, m, s));
-    std::swap(w.Ur, w.Vr);
-    std::swap(w.Ui, w.Vi);
+    // dU = Ur [Fa Fc] + Ui [Fb Fd] in FP32 (a correction of size |E|), then U += dU in FP64
+    BSE_TRY(gemm<float>(m, n, n, 1.0, w.Urf, m, false, w.Fa, n, false, 0.0, w.dUr, m, s));
+    BSE_TRY(gemm<float>(m, n, n, 1.0, w.Uif, m, false, w.Fb, n, false, 1.0, w.dUr, m, s));
+    BSE_TRY(gemm<float>(m, n, n, 1.0, w.Urf, m, false, w.Fc, n, false, 0.0, w.dUi, m, s));
+    BSE_TRY(gemm<float>(m, n, n, 1.0, w.Uif, m, false, w.Fd, n, false, 1.0, w.dUi, m, s));
+    kcount(1);
+    ref_apply<<<1024, 256, 0, s>>>((long)m * n, w.Ur, w.Ui, w.dUr, w.dUi);
+    BSE_LAUNCH_CHECK();
     ++sweeps;
   }
   kcount(1);

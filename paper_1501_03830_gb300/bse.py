@@ -43,7 +43,7 @@ EXPORTS = [
     "bse_stage_form_M", "bse_stage_potrf_worksize", "bse_stage_potrf", "bse_stage_form_W",
     "bse_stage_tridiag_worksize", "bse_stage_tridiag", "bse_debug_trace_tridiag", "bse_stage_tridiag_grid", "bse_stage_tdeig_worksize", "bse_stage_tdeig", "bse_stage_tdeig_noalloc",
     "bse_stage_backtransform_worksize", "bse_stage_backtransform", "bse_stage_weights",
-    "bse_stage_refine_worksize", "bse_stage_refine",
+    "bse_stage_refine_worksize", "bse_stage_refine", "bse_tc_gemm_bf16", "bse_ozaki_worksize", "bse_ozaki_gemm",
 ]
 
 
@@ -122,6 +122,9 @@ def lib() -> C.CDLL:
         "bse_stage_weights": (i, [i, vp, i, vp, vp, vp, vp]),
         "bse_stage_refine_worksize": (sz, [i]),
         "bse_stage_refine": (i, [i, vp, vp, vp, i, vp, vp, vp, C.POINTER(i), C.POINTER(d)]),
+        "bse_tc_gemm_bf16": (i, [i, i, i, vp, vp, i, vp, i, vp, vp]),
+        "bse_ozaki_worksize": (sz, [i, i, i, i]),
+        "bse_ozaki_gemm": (i, [i, i, i, vp, i, vp, i, vp, i, i, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

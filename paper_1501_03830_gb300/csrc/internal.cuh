@@ -32,6 +32,12 @@ int backtransform(int m, T* L, long ldl, const T* W, long ldw, const T* tau, con
 
 int weights(int n, const double* X, long ldx, const double* dr, const double* dl, double* w, cudaStream_t s);
 
+size_t ozaki_worksize(int M, int N, int K, int s);
+int ozaki_gemm(int M, int N, int K, const double* A, long lda, const double* B, long ldb, double* C, long ldc, int s,
+               void* work, bool split_A, int* status, cudaStream_t st);
+// digits per operand for a K-long FP64-accurate product (about 50 bits)
+int ozaki_digits(int K);
+
 size_t refine_worksize(int n);
 // FP64 structure-preserving refinement of (lam, X) in place (X: 2n x n complex128, ld 2n),
 // against the FP64 M (2n x 2n). Returns BSE_OK and fills the diagnostics.

@@ -46,12 +46,18 @@ struct RefWork {
   unsigned long long* maxes;  // [0] max resid, [1] max dlam (as ordered bit patterns)
   int* cid;                   // cluster id per column
   int2* clus;                 // (first column, size) per cluster
+  void* oz;                   // digit-split tensor-core product workspace
 };
+
+// The FP64-accurate M U runs on the tensor cores (digit splitting) from this size on.
+static bool refine_uses_tc(int n) { return 2 * n >= 1024; }
 
 size_t refine_worksize(int n) {
   const size_t m = 2 * (size_t)n;
-  return 4 * al256(8 * m * n) + 6 * al256(4 * m * n) + 8 * al256(4 * (size_t)n * n) + 2 * al256(8 * (size_t)n) +
-         al256(64) + al256(64) + al256(4 * (size_t)n) + al256(8 * ((size_t)n / 2 + 2));
+  size_t b = 2 * al256(16 * m * n) + 6 * al256(4 * m * n) + 8 * al256(4 * (size_t)n * n) + 2 * al256(8 * (size_t)n) +
+             al256(64) + al256(64) + al256(4 * (size_t)n) + al256(8 * ((size_t)n / 2 + 2));
+  if (refine_uses_tc(n)) b += al256(ozaki_worksize((int)m, 2 * n, (int)m, ozaki_digits((int)m)));
+  return b;
 }
 
 static RefWork carve_ref(void* work, int n) {
@@ -63,8 +69,9 @@ static RefWork carve_ref(void* work, int n) {
     p += al256(sz);
     return r;
   };
-  w.Ur = (double*)take(8 * m * n); w.Ui = (double*)take(8 * m * n);
-  w.Pr = (double*)take(8 * m * n); w.Pi = (double*)take(8 * m * n);
+  // [Ur | Ui] and [Pr | Pi] are contiguous m x 2n blocks
+  w.Ur = (double*)take(16 * m * n); w.Ui = w.Ur + m * n;
+  w.Pr = (double*)take(16 * m * n); w.Pi = w.Pr + m * n;
   w.Urf = (float*)take(4 * m * n); w.Uif = (float*)take(4 * m * n);
   w.Rrf = (float*)take(4 * m * n); w.Rif = (float*)take(4 * m * n);
   w.dUr = (float*)take(4 * m * n); w.dUi = (float*)take(4 * m * n);
@@ -78,6 +85,7 @@ static RefWork carve_ref(void* work, int n) {
   w.maxes = (unsigned long long*)take(64);
   w.cid = (int*)take(4 * (size_t)n);
   w.clus = (int2*)take(8 * ((size_t)n / 2 + 2));
+  w.oz = refine_uses_tc(n) ? take(ozaki_worksize((int)m, 2 * n, (int)m, ozaki_digits((int)m))) : nullptr;
   return w;
 }
 
@@ -481,7 +489,6 @@ static void find_clusters(const std::vector<double>& lam, double tau, std::vecto
 
 int refine(int n, const double* M, double* lam, double* X, int max_sweeps, double tol, void* work, DevStatus* st,
            cudaStream_t s, int* sweeps_done, double* resid, double* dlam_last, double* dlam_first) {
-  (void)st;
   const int m = 2 * n;
   RefWork w = carve_ref(work, n);
   const dim3 eg(ceil_div(n, 128), n);
@@ -506,9 +513,16 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
   std::vector<int> cid;
   *dlam_first = 0;
   for (int it = 0;; ++it) {
-    // P = M U
-    BSE_TRY(gemm<double>(m, n, m, 1.0, M, m, false, w.Ur, m, false, 0.0, w.Pr, m, s));
-    BSE_TRY(gemm<double>(m, n, m, 1.0, M, m, false, w.Ui, m, false, 0.0, w.Pi, m, s));
+    // P = M U, FP64-accurate: [Pr | Pi] = M [Ur | Ui]
+    if (refine_uses_tc(n)) {
+      // M is symmetric, so its column-major storage is also its K-major row layout;
+      // its digits are split once and reused by every sweep
+      BSE_TRY(ozaki_gemm(m, 2 * n, m, M, m, w.Ur, m, w.Pr, m, ozaki_digits(m), w.oz, it == 0,
+                         reinterpret_cast<int*>(st), s));
+    } else {
+      BSE_TRY(gemm<double>(m, n, m, 1.0, M, m, false, w.Ur, m, false, 0.0, w.Pr, m, s));
+      BSE_TRY(gemm<double>(m, n, m, 1.0, M, m, false, w.Ui, m, false, 0.0, w.Pi, m, s));
+    }
     BSE_CUDA(cudaMemsetAsync(w.maxes, 0, 16, s));
     kcount(1);
     ref_colstats<<<n, 256, 0, s>>>(n, w.Ur, w.Ui, w.Pr, w.Pi, w.Urf, w.Uif, w.Rrf, w.Rif, lam, w.lam_new, w.bnorm,

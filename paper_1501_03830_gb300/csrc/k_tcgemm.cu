@@ -1,0 +1,348 @@
+// Tensor-core GEMM for sm_103a: tcgen05.mma (bf16 x bf16 -> FP32 in TMEM) fed
+// by TMA, used for the FP64-accurate products of the refinement (error-free
+// digit splitting, see k_ozaki.cu) and testable on its own.
+//
+// One CTA owns a 128 x 256 output tile and runs a list of "units": unit u
+// multiplies digit matrix a_digit[u] of A by digit matrix b_digit[u] of B over
+// the whole K, accumulating in one of two TMEM accumulators (256 FP32 columns
+// each), while the epilogue drains the other. Both operands are K-major bf16
+// (A: rows x K, B: cols x K, K contiguous), staged by TMA with 128-byte
+// swizzle into a 4-stage shared-memory ring guarded by mbarriers.
+//
+// Warp roles (192 threads): warp 0 = TMA producer, warp 1 = TMEM owner and
+// MMA issuer (one thread), warps 2-5 = epilogue (TMEM lane quadrant = warp % 4).
+// Every mbarrier wait is bounded: on timeout the kernel records
+// BSE_ERR_TIMEOUT, stops issuing work, drains what it issued (bounded again),
+// frees its TMEM and returns.
+#include <cuda.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "tcgemm.cuh"
+
+namespace bse {
+namespace tc {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;  // 16 KiB
+constexpr int B_BYTES = BN * BK * 2;  // 32 KiB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int THREADS = 192;
+constexpr uint32_t TMEM_COLS = 512;  // two 128 x 256 FP32 accumulators
+constexpr long kSpin = 1L << 26;     // bounded waits (~seconds)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false (and *err set) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* err) {
+  for (long it = 0; it < kSpin; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*err) return false;
+  }
+  *err = BSE_ERR_TIMEOUT;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (rows of 64 bf16 = 128 bytes).
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading-dimension offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride-dimension offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N = 256, M = 128.
+__host__ __device__ constexpr uint32_t make_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const TcParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;  // [2]
+  uint64_t* tempty = tfull + 2;      // [2]
+  uint64_t* drain = tempty + 2;      // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_m = (P.M + BM - 1) / BM;
+  const int m0 = (blockIdx.x % tiles_m) * BM;
+  const int n0 = (blockIdx.x / tiles_m) * BN;
+  const int KB = (P.K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 128);
+    }
+    mbar_init(drain, 1);
+    *err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer
+      int it = 0;
+      for (int u = 0; u < P.units && !*err; ++u) {
+        const int ya = P.a_digit[u] * P.a_rows + m0;
+        const int yb = P.b_digit[u] * P.b_rows + n0;
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const int st = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1;
+          if (!mbar_wait(&empty[st], ph ^ 1, err)) break;
+          uint8_t* sa = smem + st * STAGE_BYTES;
+          mbar_expect_tx(&full[st], STAGE_BYTES);
+          tma_load_2d(sa, &tmA, kb * BK, ya, &full[st]);
+          tma_load_2d(sa + A_BYTES, &tmB, kb * BK, yb, &full[st]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      const uint32_t idesc = make_idesc();
+      int it = 0;
+      bool ok = true;
+      for (int u = 0; u < P.units && ok; ++u) {
+        const int buf = u & 1;
+        const uint32_t uph = (u >> 1) & 1;
+        ok = mbar_wait(&tempty[buf], uph ^ 1, err);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t d = tmem_base + (uint32_t)(buf * BN);
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const int st = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1;
+          ok = mbar_wait(&full[st], ph, err);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
+          const uint64_t da = make_desc(sa), db = make_desc(sa + A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            umma_bf16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, (kb | kk) != 0);
+          umma_commit(&empty[st]);
+        }
+        if (ok) umma_commit(&tfull[buf]);
+      }
+      // all issued MMAs complete before TMEM can be released
+      umma_commit(drain);
+      for (long w = 0; w < kSpin && !mbar_try_wait(drain, 0); ++w) {
+      }
+    }
+  } else {
+    // epilogue: TMEM lane quadrant q4 = warp % 4, one output row per thread
+    const int q4 = warp & 3;
+    const int row = m0 + q4 * 32 + lane;
+    for (int u = 0; u < P.units; ++u) {
+      const int buf = u & 1;
+      const uint32_t uph = (u >> 1) & 1;
+      // warp-uniform wait: tcgen05.ld below needs every lane
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], uph, err));
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t tb = tmem_base + (uint32_t)(buf * BN) + ((uint32_t)(q4 * 32) << 16);
+      const double ps = P.unit_scale[u];
+      const double rsc = (P.mode == 1 && row < P.M) ? P.rs[row] * ps : 0.0;
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tb + (uint32_t)c0, v);
+        if (row < P.M) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int col = n0 + c0 + i;
+            if (col < P.N) {
+              if (P.mode == 0) {
+                P.Cf[row + (long)col * P.ldc] = v[i];
+              } else {
+                double* cp = P.Cd + row + (long)col * P.ldc;
+                *cp = fma((double)v[i], rsc * P.cs[col], *cp);
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[buf]);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+  if (threadIdx.x == 0 && *err && P.status) atomicCAS(P.status, 0, *err);
+}
+
+// ---- host side -------------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// rows x K bf16, K contiguous with row pitch ldk (elements); box BK x box_rows.
+static int make_map(CUtensorMap* map, const void* base, long rows, long K, long ldk, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    record_message("cuTensorMapEncodeTiled is not available");
+    return BSE_ERR_CUDA;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ldk * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    record_message("cuTensorMapEncodeTiled failed");
+    return BSE_ERR_CUDA;
+  }
+  return BSE_OK;
+}
+
+int tc_gemm(const TcProblem& pb, cudaStream_t s) {
+  if (pb.M <= 0 || pb.N <= 0 || pb.K <= 0 || pb.units <= 0) return BSE_OK;
+  if (pb.units > kMaxUnits || (pb.ldk % 8) != 0 || (reinterpret_cast<uintptr_t>(pb.A) % 16) != 0 ||
+      (reinterpret_cast<uintptr_t>(pb.B) % 16) != 0) {
+    record_message("tc_gemm: bad layout (K pitch must be a multiple of 8, bases 16-byte aligned)");
+    return BSE_ERR_ARG;
+  }
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  if (attr_err != cudaSuccess) {
+    record_error("cudaFuncSetAttribute(tc_gemm_kernel)", attr_err, __FILE__, __LINE__);
+    return BSE_ERR_CUDA;
+  }
+  CUtensorMap ma, mb;
+  BSE_TRY(make_map(&ma, pb.A, (long)pb.a_rows * pb.a_digits, pb.K, pb.ldk, BM));
+  BSE_TRY(make_map(&mb, pb.B, (long)pb.b_rows * pb.b_digits, pb.K, pb.ldk, BN));
+  TcParams P{};
+  P.M = pb.M; P.N = pb.N; P.K = pb.K;
+  P.a_rows = pb.a_rows; P.b_rows = pb.b_rows;
+  P.units = pb.units;
+  for (int u = 0; u < pb.units; ++u) {
+    P.a_digit[u] = pb.a_digit[u];
+    P.b_digit[u] = pb.b_digit[u];
+    P.unit_scale[u] = pb.unit_scale[u];
+  }
+  P.mode = pb.mode; P.Cf = pb.Cf; P.Cd = pb.Cd; P.ldc = pb.ldc; P.rs = pb.rs; P.cs = pb.cs;
+  P.status = pb.status;
+  const long tiles = (long)((pb.M + BM - 1) / BM) * ((pb.N + BN - 1) / BN);
+  KprofScope ks(K_GEMM_TC, s, 0.0, 2.0 * pb.M * (double)pb.N * pb.K * pb.units);
+  tc_gemm_kernel<<<(unsigned)tiles, THREADS, SMEM_BYTES, s>>>(ma, mb, P);
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
+}  // namespace tc
+}  // namespace bse
+
+// C (M x N, FP32, column-major, ldc) = A (M x K bf16, K-major with pitch ldk) *
+// B (N x K bf16, K-major with pitch ldk)^T on the tensor cores.
+extern "C" int bse_tc_gemm_bf16(int M, int N, int K, const void* A, const void* B, int ldk, float* C, int ldc,
+                                int* dev_status, void* stream) {
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C || ldk < K || ldc < M || !dev_status) return BSE_ERR_ARG;
+  bse::tc::TcProblem pb{};
+  pb.M = M; pb.N = N; pb.K = K; pb.ldk = ldk;
+  pb.A = A; pb.B = B; pb.a_rows = M; pb.b_rows = N; pb.a_digits = 1; pb.b_digits = 1;
+  pb.units = 1; pb.a_digit[0] = 0; pb.b_digit[0] = 0; pb.unit_scale[0] = 1.0;
+  pb.mode = 0; pb.Cf = C; pb.ldc = ldc; pb.status = dev_status;
+  return bse::tc::tc_gemm(pb, (cudaStream_t)stream);
+}

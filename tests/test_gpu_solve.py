@@ -53,7 +53,7 @@ def test_fp64_vs_oracle(n):
     ctx.close()
 
 
-@pytest.mark.parametrize("n", [1, 7, 64, 150])
+@pytest.mark.parametrize("n", [1, 7, 64, 150, 600])
 def test_mixed_and_refined(n):
     torch_cuda()
     bse, ctx = _ctx()

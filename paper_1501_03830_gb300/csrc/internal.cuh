@@ -33,6 +33,16 @@ int backtransform(int m, T* L, long ldl, const T* W, long ldw, const T* tau, con
 int weights(int n, const double* X, long ldx, const double* dr, const double* dl, double* w, cudaStream_t s);
 
 size_t ozaki_worksize(int M, int N, int K, int s);
+// an operand of the digit-split product: K-vectors at ptr + v*ld (strided = false)
+// or at ptr + v with stride ld between consecutive k (strided = true)
+struct OzOperand {
+  const void* ptr;
+  long ld;
+  bool strided;
+  bool f32;
+};
+int ozaki_gemm_ex(const OzOperand& A, const OzOperand& B, int M, int N, int K, double* C, long ldc, int s,
+                  bool accumulate, void* work, bool split_A, int* status, cudaStream_t st);
 int ozaki_gemm(int M, int N, int K, const double* A, long lda, const double* B, long ldb, double* C, long ldc, int s,
                void* work, bool split_A, int* status, cudaStream_t st);
 // digits per operand for a K-long FP64-accurate product (about 50 bits)

@@ -22,6 +22,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "internal.cuh"
 #include "tcgemm.cuh"
 
 namespace bse {
@@ -58,14 +59,16 @@ size_t ozaki_worksize(int M, int N, int K, int s) {
 }
 
 // One block per K-vector (row of A or column of B): power-of-two scale and digits.
-__global__ void __launch_bounds__(256) ozaki_split(const double* __restrict__ X, long ldx, int K, int ldk, int beta,
+// Vector v is X[v * ldx + k] (k contiguous).
+template <typename TI>
+__global__ void __launch_bounds__(256) ozaki_split(const TI* __restrict__ X, long ldx, int K, int ldk, int beta,
                                                    int s, long digit_stride, __nv_bfloat16* __restrict__ D,
                                                    double* __restrict__ scale) {
   __shared__ double red[8];
   const long v = blockIdx.x;
-  const double* x = X + v * ldx;
+  const TI* x = X + v * ldx;
   double mx = 0.0;
-  for (int k = threadIdx.x; k < K; k += 256) mx = fmax(mx, fabs(x[k]));
+  for (int k = threadIdx.x; k < K; k += 256) mx = fmax(mx, fabs((double)x[k]));
   for (int o = 16; o >= 1; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
@@ -76,7 +79,7 @@ __global__ void __launch_bounds__(256) ozaki_split(const double* __restrict__ X,
   if (threadIdx.x == 0) scale[v] = ldexp(1.0, e);
   __nv_bfloat16* dv = D + v * (long)ldk;
   for (int k = threadIdx.x; k < ldk; k += 256) {
-    double r = (k < K && mx > 0.0) ? ldexp(x[k], -e) : 0.0;
+    double r = (k < K && mx > 0.0) ? ldexp((double)x[k], -e) : 0.0;
     for (int p = 0; p < s; ++p) {
       const double t = ldexp(r, beta);
       const double d = rint(t);
@@ -86,9 +89,69 @@ __global__ void __launch_bounds__(256) ozaki_split(const double* __restrict__ X,
   }
 }
 
-// C (M x N, column-major, ldc) = A B to FP64 accuracy. work: ozaki_worksize bytes.
-int ozaki_gemm(int M, int N, int K, const double* A, long lda, const double* B, long ldb, double* C, long ldc, int s,
-               void* work, bool split_A, int* status, cudaStream_t st) {
+// Same for vectors stored with stride: vector v is X[v + k * ldx] (rows of a
+// column-major matrix). 32 vectors per block, staged through shared memory so
+// reads and digit writes are both coalesced.
+template <typename TI>
+__global__ void __launch_bounds__(256) ozaki_split_rows(const TI* __restrict__ X, long ldx, int V, int K, int ldk,
+                                                        int beta, int s, long digit_stride,
+                                                        __nv_bfloat16* __restrict__ D, double* __restrict__ scale) {
+  __shared__ double tile[64][33];
+  __shared__ double vmax[8][32];
+  __shared__ int vexp[32];
+  const int v0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 x 32
+  // pass 1: per-vector max
+  double mx = 0.0;
+  if (v0 + tx < V)
+    for (int k = ty; k < K; k += 8) mx = fmax(mx, fabs((double)X[(v0 + tx) + (long)k * ldx]));
+  vmax[ty][tx] = mx;
+  __syncthreads();
+  if (ty == 0) {
+    double m2 = 0.0;
+    for (int w = 0; w < 8; ++w) m2 = fmax(m2, vmax[w][tx]);
+    int e = 0;
+    if (m2 > 0.0) frexp(m2, &e);
+    vexp[tx] = (m2 > 0.0) ? e : 1000000;  // 1e6 marks an all-zero vector
+    if (v0 + tx < V) scale[v0 + tx] = ldexp(1.0, m2 > 0.0 ? e : 0);
+  }
+  __syncthreads();
+  // pass 2: digits, 64 k at a time
+  for (int k0 = 0; k0 < ldk; k0 += 64) {
+    for (int kk = ty; kk < 64; kk += 8) {
+      const int k = k0 + kk;
+      tile[kk][tx] = (v0 + tx < V && k < K) ? (double)X[(v0 + tx) + (long)k * ldx] : 0.0;
+    }
+    __syncthreads();
+    // thread (ty, tx) writes vectors ty, ty+8, ... at k = k0 + 2 tx, k0 + 2 tx + 1
+    for (int vv = ty; vv < 32; vv += 8) {
+      if (v0 + vv >= V) continue;
+      const int e = vexp[vv];
+      __nv_bfloat16* dv = D + (long)(v0 + vv) * ldk + k0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int kk = 2 * tx + h;
+        double r = (e == 1000000) ? 0.0 : ldexp(tile[kk][vv], -e);
+        for (int p = 0; p < s; ++p) {
+          const double t = ldexp(r, beta);
+          const double d = rint(t);
+          r = t - d;
+          dv[p * digit_stride + kk] = __float2bfloat16_rn((float)d);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Generic digit-split product C (M x N, column-major, ldc) (+)= A B on the
+// tensor cores. Operand descriptions: A rows are K-vectors at A + i*lda
+// (a_rows_strided: A[i + k*lda] instead), B columns are K-vectors at B + j*ldb
+// (b_strided: B[j + k*ldb]); element types double or float (a_f32 / b_f32).
+// accumulate: add to C instead of overwriting it. split_A = false reuses the A
+// digits already in the workspace (same A, same K, same s).
+int ozaki_gemm_ex(const OzOperand& A, const OzOperand& B, int M, int N, int K, double* C, long ldc, int s,
+                  bool accumulate, void* work, bool split_A, int* status, cudaStream_t st) {
   if (M <= 0 || N <= 0) return BSE_OK;
   if (s < 1 || s * (s + 1) / 2 > tc::kMaxUnits) return BSE_ERR_ARG;
   const OzakiPlan p = plan(M, N, K, s);
@@ -100,17 +163,30 @@ int ozaki_gemm(int M, int N, int K, const double* A, long lda, const double* B, 
   double* rs = reinterpret_cast<double*>(w);
   w += al256o(8 * (size_t)M);
   double* cs = reinterpret_cast<double*>(w);
-  if (split_A) {
-    KprofScope ks(K_ELEMENTWISE, st, 8.0 * M * (double)K + 2.0 * s * M * (double)p.ldk, 0.0);
-    ozaki_split<<<M, 256, 0, st>>>(A, lda, K, p.ldk, p.beta, s, (long)M * p.ldk, dA, rs);
-  }
-  BSE_LAUNCH_CHECK();
-  {
-    KprofScope ks(K_ELEMENTWISE, st, 8.0 * N * (double)K + 2.0 * s * N * (double)p.ldk, 0.0);
-    ozaki_split<<<N, 256, 0, st>>>(B, ldb, K, p.ldk, p.beta, s, (long)N * p.ldk, dB, cs);
-  }
-  BSE_LAUNCH_CHECK();
-  BSE_CUDA(cudaMemset2DAsync(C, ldc * sizeof(double), 0, (size_t)M * sizeof(double), N, st));
+  auto split = [&](const OzOperand& X, int V, __nv_bfloat16* D, double* scl) -> int {
+    const double bytes = (X.f32 ? 4.0 : 8.0) * V * (double)K + 2.0 * s * V * (double)p.ldk;
+    KprofScope ks(K_ELEMENTWISE, st, bytes, 0.0);
+    const long dstride = (long)V * p.ldk;
+    if (!X.strided) {
+      if (X.f32)
+        ozaki_split<float><<<V, 256, 0, st>>>((const float*)X.ptr, X.ld, K, p.ldk, p.beta, s, dstride, D, scl);
+      else
+        ozaki_split<double><<<V, 256, 0, st>>>((const double*)X.ptr, X.ld, K, p.ldk, p.beta, s, dstride, D, scl);
+    } else {
+      const int blocks = ceil_div(V, 32);
+      if (X.f32)
+        ozaki_split_rows<float><<<blocks, 256, 0, st>>>((const float*)X.ptr, X.ld, V, K, p.ldk, p.beta, s, dstride, D,
+                                                        scl);
+      else
+        ozaki_split_rows<double><<<blocks, 256, 0, st>>>((const double*)X.ptr, X.ld, V, K, p.ldk, p.beta, s, dstride,
+                                                         D, scl);
+    }
+    BSE_LAUNCH_CHECK();
+    return BSE_OK;
+  };
+  if (split_A) BSE_TRY(split(A, M, dA, rs));
+  BSE_TRY(split(B, N, dB, cs));
+  if (!accumulate) BSE_CUDA(cudaMemset2DAsync(C, ldc * sizeof(double), 0, (size_t)M * sizeof(double), N, st));
   tc::TcProblem pb{};
   pb.M = M; pb.N = N; pb.K = K; pb.ldk = p.ldk;
   pb.A = dA; pb.B = dB; pb.a_rows = M; pb.b_rows = N; pb.a_digits = s; pb.b_digits = s;
@@ -125,6 +201,13 @@ int ozaki_gemm(int M, int N, int K, const double* A, long lda, const double* B, 
   pb.units = u;
   pb.mode = 1; pb.Cd = C; pb.ldc = ldc; pb.rs = rs; pb.cs = cs; pb.status = status;
   return tc::tc_gemm(pb, st);
+}
+
+// C (M x N, column-major, ldc) = A B to FP64 accuracy. work: ozaki_worksize bytes.
+int ozaki_gemm(int M, int N, int K, const double* A, long lda, const double* B, long ldb, double* C, long ldc, int s,
+               void* work, bool split_A, int* status, cudaStream_t st) {
+  OzOperand a{A, lda, false, false}, b{B, ldb, false, false};
+  return ozaki_gemm_ex(a, b, M, N, K, C, ldc, s, false, work, split_A, status, st);
 }
 
 }  // namespace bse

@@ -25,6 +25,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <utility>
 #include <vector>
 
@@ -46,8 +47,12 @@ struct RefWork {
   unsigned long long* maxes;  // [0] max resid, [1] max dlam (as ordered bit patterns)
   int* cid;                   // cluster id per column
   int2* clus;                 // (first column, size) per cluster
-  void* oz;                   // digit-split tensor-core product workspace
+  void* oz;                   // digit-split tensor-core product workspace (M U)
+  void* oz2;                  // same for the projections and the update
+  double* Gbig;               // 2n x 2n: [Ur Ui]^T [Rr Ri]
 };
+
+constexpr int kRefineCorrDigits = 5;  // ~25 bits for correction-sized products
 
 // The FP64-accurate M U runs on the tensor cores (digit splitting) from this size on.
 static bool refine_uses_tc(int n) { return 2 * n >= 1024; }
@@ -56,7 +61,11 @@ size_t refine_worksize(int n) {
   const size_t m = 2 * (size_t)n;
   size_t b = 2 * al256(16 * m * n) + 6 * al256(4 * m * n) + 8 * al256(4 * (size_t)n * n) + 2 * al256(8 * (size_t)n) +
              al256(64) + al256(64) + al256(4 * (size_t)n) + al256(8 * ((size_t)n / 2 + 2));
-  if (refine_uses_tc(n)) b += al256(ozaki_worksize((int)m, 2 * n, (int)m, ozaki_digits((int)m)));
+  if (refine_uses_tc(n)) {
+    b += al256(ozaki_worksize((int)m, 2 * n, (int)m, ozaki_digits((int)m)));
+    b += al256(ozaki_worksize(2 * n, 2 * n, (int)m, kRefineCorrDigits));
+    b += al256(8 * (size_t)4 * n * n);
+  }
   return b;
 }
 
@@ -73,7 +82,7 @@ static RefWork carve_ref(void* work, int n) {
   w.Ur = (double*)take(16 * m * n); w.Ui = w.Ur + m * n;
   w.Pr = (double*)take(16 * m * n); w.Pi = w.Pr + m * n;
   w.Urf = (float*)take(4 * m * n); w.Uif = (float*)take(4 * m * n);
-  w.Rrf = (float*)take(4 * m * n); w.Rif = (float*)take(4 * m * n);
+  w.Rrf = (float*)take(8 * m * n); w.Rif = w.Rrf + m * n;  // [Rrf | Rif] contiguous
   w.dUr = (float*)take(4 * m * n); w.dUi = (float*)take(4 * m * n);
   w.G1 = (float*)take(4 * (size_t)n * n); w.G2 = (float*)take(4 * (size_t)n * n);
   w.G3 = (float*)take(4 * (size_t)n * n); w.G4 = (float*)take(4 * (size_t)n * n);
@@ -85,7 +94,13 @@ static RefWork carve_ref(void* work, int n) {
   w.maxes = (unsigned long long*)take(64);
   w.cid = (int*)take(4 * (size_t)n);
   w.clus = (int2*)take(8 * ((size_t)n / 2 + 2));
-  w.oz = refine_uses_tc(n) ? take(ozaki_worksize((int)m, 2 * n, (int)m, ozaki_digits((int)m))) : nullptr;
+  w.oz = w.oz2 = nullptr;
+  w.Gbig = nullptr;
+  if (refine_uses_tc(n)) {
+    w.oz = take(ozaki_worksize((int)m, 2 * n, (int)m, ozaki_digits((int)m)));
+    w.oz2 = take(ozaki_worksize(2 * n, 2 * n, (int)m, kRefineCorrDigits));
+    w.Gbig = (double*)take(8 * (size_t)4 * n * n);
+  }
   return w;
 }
 
@@ -217,6 +232,39 @@ __global__ void ref_buildE(int n, const float* __restrict__ G1, const float* __r
   }
   const double s = -1.0 / (li + lj);
   const double e2r = c2r * s, e2i = c2i * s;
+  Fa[k] = (float)(e1r + e2r);
+  Fb[k] = (float)(e2i - e1i);
+  Fc[k] = (float)(e1i + e2i);
+  Fd[k] = (float)(e1r - e2r);
+}
+
+// E from G = [Ur Ui]^T [Rr Ri] (2n x 2n, FP64); writes the FP32 coefficient blocks
+// Fa, Fb, Fc, Fd (n x n) of the update U <- U + U E11 + conj(U) E21.
+__global__ void ref_buildE_big(int n, const double* __restrict__ G, const double* __restrict__ lam,
+                               const double* __restrict__ bnorm, const int* __restrict__ cluster_id,
+                               float* __restrict__ Fa, float* __restrict__ Fb, float* __restrict__ Fc,
+                               float* __restrict__ Fd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= n) return;
+  const long ld = 2L * n;
+  const double g1 = G[i + (long)j * ld], g3 = G[i + (long)(n + j) * ld];
+  const double g4 = G[n + i + (long)j * ld], g2 = G[n + i + (long)(n + j) * ld];
+  const double c1r = g1 + g2, c1i = g3 - g4;
+  const double c2r = g1 - g2, c2i = g3 + g4;
+  const double li = lam[i], lj = lam[j];
+  double e1r = 0.0, e1i = 0.0;
+  if (i == j) {
+    e1r = 0.5 * (1.0 - bnorm[j]);
+  } else {
+    const double d = lj - li;
+    if (cluster_id[i] != cluster_id[j] && fabs(d) > 1e-14 * fmax(fabs(li), fabs(lj))) {
+      e1r = c1r / d;
+      e1i = c1i / d;
+    }
+  }
+  const double sc = -1.0 / (li + lj);
+  const double e2r = c2r * sc, e2i = c2i * sc;
+  const long k = i + (long)j * n;
   Fa[k] = (float)(e1r + e2r);
   Fb[k] = (float)(e2i - e1i);
   Fc[k] = (float)(e1i + e2i);
@@ -562,15 +610,29 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     // the host vectors must outlive the asynchronous uploads above
     BSE_CUDA(cudaStreamSynchronize(s));
     if (verbose) fprintf(stderr, "[bse refine] n=%d sweep %d: %zu clusters (tau %.1e)\n", n, it, clusters.size(), tau);
-    // C1 = U^H R, C2 = U^T R from four real FP32 products (R is residual-sized, so FP32
-    // rounding of these products is eps32 relative to a quantity that is itself small)
-    BSE_TRY(gemm<float>(n, n, m, 1.0, w.Urf, m, true, w.Rrf, m, false, 0.0, w.G1, n, s));
-    BSE_TRY(gemm<float>(n, n, m, 1.0, w.Uif, m, true, w.Rif, m, false, 0.0, w.G2, n, s));
-    BSE_TRY(gemm<float>(n, n, m, 1.0, w.Urf, m, true, w.Rif, m, false, 0.0, w.G3, n, s));
-    BSE_TRY(gemm<float>(n, n, m, 1.0, w.Uif, m, true, w.Rrf, m, false, 0.0, w.G4, n, s));
-    kcount(1);
-    ref_buildE<<<eg, 128, 0, s>>>(n, w.G1, w.G2, w.G3, w.G4, lam, w.bnorm, w.cid, w.Fa, w.Fb, w.Fc, w.Fd);
-    BSE_LAUNCH_CHECK();
+    if (refine_uses_tc(n)) {
+      // tensor cores: C1 = U^H R and C2 = U^T R from the one real 2n x 2n product
+      // G = [Ur Ui]^T [Rr Ri]; each operand column (an eigenvector, a residual) has a
+      // uniform scale, so ~25-bit digits carry these residual-sized products fully
+      OzOperand ua{w.Ur, m, false, false}, rb{w.Rrf, m, false, true};
+      BSE_TRY(ozaki_gemm_ex(ua, rb, 2 * n, 2 * n, m, w.Gbig, 2 * n, kRefineCorrDigits, false, w.oz2, true,
+                            reinterpret_cast<int*>(st), s));
+      kcount(1);
+      ref_buildE_big<<<eg, 128, 0, s>>>(n, w.Gbig, lam, w.bnorm, w.cid, w.Fa, w.Fb, w.Fc, w.Fd);
+      BSE_LAUNCH_CHECK();
+    } else {
+      // C1 = U^H R, C2 = U^T R from four real FP32 products (R is residual-sized, so FP32
+      // rounding of these products is eps32 relative to a quantity that is itself small)
+      BSE_TRY(gemm<float>(n, n, m, 1.0, w.Urf, m, true, w.Rrf, m, false, 0.0, w.G1, n, s));
+      BSE_TRY(gemm<float>(n, n, m, 1.0, w.Uif, m, true, w.Rif, m, false, 0.0, w.G2, n, s));
+      BSE_TRY(gemm<float>(n, n, m, 1.0, w.Urf, m, true, w.Rif, m, false, 0.0, w.G3, n, s));
+      BSE_TRY(gemm<float>(n, n, m, 1.0, w.Uif, m, true, w.Rrf, m, false, 0.0, w.G4, n, s));
+      kcount(1);
+      ref_buildE<<<eg, 128, 0, s>>>(n, w.G1, w.G2, w.G3, w.G4, lam, w.bnorm, w.cid, w.Fa, w.Fb, w.Fc, w.Fd);
+      BSE_LAUNCH_CHECK();
+    }
+    // the update keeps FP32 entries (not column-scaled digits): a column of F mixes one
+    // near-cluster coefficient with many tiny ones, and each of them needs its own bits
     // dU = Ur [Fa Fc] + Ui [Fb Fd] in FP32 (a correction of size |E|), then U += dU in FP64
     BSE_TRY(gemm<float>(m, n, n, 1.0, w.Urf, m, false, w.Fa, n, false, 0.0, w.dUr, m, s));
     BSE_TRY(gemm<float>(m, n, n, 1.0, w.Uif, m, false, w.Fb, n, false, 1.0, w.dUr, m, s));

@@ -130,9 +130,17 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // grouped tile order: consecutive blocks cover a band of kGroupM row tiles, so
+  // the ~150 co-resident CTAs share their A rows and B columns through L2
+  constexpr int kGroupM = 16;
   const int tiles_m = (P.M + BM - 1) / BM;
-  const int m0 = (blockIdx.x % tiles_m) * BM;
-  const int n0 = (blockIdx.x / tiles_m) * BN;
+  const int tiles_n = (P.N + BN - 1) / BN;
+  const int group = blockIdx.x / (kGroupM * tiles_n);
+  const int first_m = group * kGroupM;
+  const int gm = min(kGroupM, tiles_m - first_m);
+  const int in_group = blockIdx.x - group * kGroupM * tiles_n;
+  const int m0 = (first_m + in_group % gm) * BM;
+  const int n0 = (in_group / gm) * BN;
   const int KB = (P.K + BK - 1) / BK;
 
   if (threadIdx.x == 0) {

@@ -142,6 +142,23 @@ size_t bse_ozaki_worksize(int M, int N, int K, int s);
 int bse_ozaki_gemm(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C, int ldc, int s,
                    void* work, int* dev_status, void* stream);
 
+/* C (M x N FP32, column-major, ldc) = alpha op(A) op(B) + beta C on the tcgen05
+ * tensor cores (kind::tf32), op(X) = X or X^T (trans flags), all column-major.
+ * split = 1: 3xTF32 -- each operand value x = hi + lo with hi = x rounded to TF32
+ * and lo = x - hi, accumulating hi*hi + hi*lo + lo*hi in FP32 (FP32-level
+ * accuracy); split = 0: one TF32 pass. uplo = 1 (2) writes only C(i,j) with i >= j
+ * (i > j) and needs M == N; 0 writes all of C. A and B need 16-byte aligned bases
+ * and leading dimensions divisible by 4 (TMA pitch rule), else BSE_ERR_ARG. A
+ * bounded internal wait that gives up stores BSE_ERR_TIMEOUT in dev_status. This
+ * is the kernel behind the FP32 products of the mixed path. */
+int bse_tc32_gemm(int M, int N, int K, float alpha, const float* A, int lda, int transA, const float* B, int ldb,
+                  int transB, float beta, float* C, int ldc, int uplo, int split, int* dev_status, void* stream);
+
+/* Engine of the FP32 products inside the mixed path: 1 (default) = the 3xTF32
+ * tensor-core kernel above wherever the operand layout allows it, 0 = the SIMT
+ * FP32 kernel everywhere (for comparisons). Process-wide. */
+int bse_set_fp32_gemm(int mode);
+
 #ifdef __cplusplus
 }
 #endif

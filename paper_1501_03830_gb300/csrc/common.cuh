@@ -23,6 +23,16 @@ __device__ __forceinline__ void set_status(DevStatus* st, int code, int info) {
   if (atomicCAS(&st->code, 0, code) == 0) st->info = info;
 }
 
+// The status word of the solve running on this host thread, for kernels whose
+// launchers take none (the tensor-core GEMM behind gemm<float>): a bounded wait
+// that gives up records there. Set for the duration of a call by StatusScope.
+DevStatus*& current_status();
+struct StatusScope {
+  DevStatus* prev;
+  explicit StatusScope(DevStatus* st) : prev(current_status()) { current_status() = st; }
+  ~StatusScope() { current_status() = prev; }
+};
+
 template <typename T>
 struct Eps;
 template <>

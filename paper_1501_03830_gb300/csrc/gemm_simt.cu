@@ -1,6 +1,7 @@
 // Host launchers for the SIMT GEMM (FP64: 64x64x16 tiles, 4x4 per thread;
 // FP32: 128x128x16 tiles, 8x8 per thread; 256 threads per CTA).
 #include "gemm_simt.cuh"
+#include "tc32.cuh"
 
 namespace bse {
 
@@ -34,8 +35,13 @@ int gemm<double>(const GemmArgs& g, cudaStream_t s) {
   return launch_gemm<double, 64, 64, 16, 4, 4>(g, s);
 }
 
+// FP32: the 3xTF32 tensor-core kernel takes every product it can lay out
+// (aligned operands, no triangular masks) that is large enough to fill the GPU;
+// the rest runs on the SIMT kernel.
 template <>
 int gemm<float>(const GemmArgs& g, cudaStream_t s) {
+  if (tc32::mode() == 1 && (double)g.M * g.N * (double)g.K >= (double)(1 << 21) && tc32::eligible(g))
+    return tc32::gemm(g, 1, nullptr, s);
   return launch_gemm<float, 128, 128, 16, 8, 8>(g, s);
 }
 

@@ -20,10 +20,19 @@
 namespace bse {
 
 constexpr int BT_NB = 64;
+// rows of V per block of the Gram kernel (33 KiB of shared memory either way)
+template <typename T>
+constexpr int gram_rows() { return sizeof(T) == 4 ? 128 : 64; }
+
+// Panel buffers (Vb, Z, Z2) have a leading dimension of m rounded up to 32 and the
+// FP32 copy of Vs a row pitch of n rounded up to 32, so that every operand of the
+// tensor-core products starts on a 16-byte boundary with a pitch divisible by 4.
+static inline long bt_ld(long x) { return (x + 31) / 32 * 32; }
 
 template <typename T>
 struct BtWork {
-  T *Vb, *Z, *Z2, *G, *Tf, *Fre, *Fim, *Vsf;
+  T *Vb, *Z, *Z2, *G, *Gpart, *Tf, *Fre, *Fim, *Vsf;
+  long ldv, ldvs;
 };
 
 static inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -31,37 +40,81 @@ static inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 template <typename T>
 size_t bt_worksize(int m) {
   const size_t n = m / 2;
-  size_t b = 3 * al256(sizeof(T) * (size_t)m * BT_NB) + 2 * al256(sizeof(T) * BT_NB * BT_NB);
+  const size_t ldv = bt_ld(m), parts = (size_t)ceil_div(m, gram_rows<T>());
+  size_t b = 3 * al256(sizeof(T) * ldv * BT_NB) + 2 * al256(sizeof(T) * BT_NB * BT_NB);
+  b += al256(sizeof(double) * parts * BT_NB * BT_NB);
   b += 2 * al256(sizeof(T) * (size_t)m * n);
-  if (sizeof(T) == 4) b += al256(sizeof(T) * (size_t)m * n);
+  if (sizeof(T) == 4) b += al256(sizeof(T) * (size_t)m * bt_ld(n));
   return b;
 }
 
 template <typename T>
 static BtWork<T> carve_bt(void* work, int m) {
   const size_t n = m / 2;
-  char* p = reinterpret_cast<char*>(work);
   BtWork<T> w;
-  w.Vb = (T*)p; p += al256(sizeof(T) * (size_t)m * BT_NB);
-  w.Z = (T*)p; p += al256(sizeof(T) * (size_t)m * BT_NB);
-  w.Z2 = (T*)p; p += al256(sizeof(T) * (size_t)m * BT_NB);
+  w.ldv = bt_ld(m);
+  w.ldvs = sizeof(T) == 4 ? bt_ld(n) : (long)n;
+  const size_t parts = (size_t)ceil_div(m, gram_rows<T>());
+  char* p = reinterpret_cast<char*>(work);
+  w.Vb = (T*)p; p += al256(sizeof(T) * w.ldv * BT_NB);
+  w.Z = (T*)p; p += al256(sizeof(T) * w.ldv * BT_NB);
+  w.Z2 = (T*)p; p += al256(sizeof(T) * w.ldv * BT_NB);
   w.G = (T*)p; p += al256(sizeof(T) * BT_NB * BT_NB);
   w.Tf = (T*)p; p += al256(sizeof(T) * BT_NB * BT_NB);
+  w.Gpart = (T*)p; p += al256(sizeof(double) * parts * BT_NB * BT_NB);
   w.Fre = (T*)p; p += al256(sizeof(T) * (size_t)m * n);
   w.Fim = (T*)p; p += al256(sizeof(T) * (size_t)m * n);
   w.Vsf = (sizeof(T) == 4) ? (T*)p : nullptr;
   return w;
 }
 
-// Vb[r, t] = v_{j0+t}[r] = W[r, j0+t] for r >= j0+t+1, else 0.
+// Panel of reflectors j0 .. j0+nbp-1 restricted to rows j0+1 .. m-1 (they are
+// zero above): Vb[r, t] = v_{j0+t}[j0+1+r] = W[j0+1+r, j0+t] for r >= t, else 0.
 template <typename T>
-__global__ void bt_copy_panel(int m, int j0, int nbp, const T* __restrict__ W, long ldw, T* __restrict__ Vb) {
+__global__ void bt_copy_panel(int m, int j0, int nbp, const T* __restrict__ W, long ldw, T* __restrict__ Vb,
+                              long ldv) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
-  if (r >= m) return;
+  if (r >= ldv) return;
   T v = T(0);
-  if (t < nbp && r >= j0 + t + 1) v = W[r + (long)(j0 + t) * ldw];
-  Vb[r + (long)t * m] = v;
+  if (t < nbp && r >= t && j0 + 1 + r < m) v = W[j0 + 1 + r + (long)(j0 + t) * ldw];
+  Vb[r + (long)t * ldv] = v;
+}
+
+// G = V^T V over row blocks: block b writes the partial Gram matrix of its
+// gram_rows<T>() rows (accumulated in T); bt_gram_sum adds the partials in FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) bt_gram_part(int rows, const T* __restrict__ Vb, long ldv,
+                                                     double* __restrict__ Gpart) {
+  constexpr int R = gram_rows<T>();
+  __shared__ T sV[R][BT_NB + 1];
+  const int r0 = blockIdx.x * R;
+  for (int e = threadIdx.x; e < R * BT_NB; e += 256) {
+    const int r = e % R, c = e / R;
+    sV[r][c] = (r0 + r < rows) ? Vb[r0 + r + (long)c * ldv] : T(0);
+  }
+  __syncthreads();
+  const int i = threadIdx.x & 63, jb = threadIdx.x >> 6;  // columns jb, jb+4, ..., jb+60
+  T acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = T(0);
+  for (int r = 0; r < R; ++r) {
+    const T vi = sV[r][i];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = fma(vi, sV[r][jb + 4 * q], acc[q]);
+  }
+  double* out = Gpart + (size_t)blockIdx.x * BT_NB * BT_NB;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) out[i + (jb + 4 * q) * BT_NB] = (double)acc[q];
+}
+
+template <typename T>
+__global__ void bt_gram_sum(int parts, const double* __restrict__ Gpart, T* __restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= BT_NB * BT_NB) return;
+  double s = 0.0;
+  for (int b = 0; b < parts; ++b) s += Gpart[(size_t)b * BT_NB * BT_NB + e];
+  G[e] = (T)s;
 }
 
 // Forward, column-wise triangular factor of a block of reflectors (the
@@ -96,10 +149,14 @@ __global__ void bt_zero_upper(int m, T* __restrict__ L, long ldl) {
   if (i < j) L[i + (long)j * ldl] = T(0);
 }
 
+// dst (rows x cols, row pitch ldd) = src (rows x cols, row pitch cols), converted.
 template <typename T>
-__global__ void to_float_kernel(long count, const double* __restrict__ src, T* __restrict__ dst) {
+__global__ void to_float_kernel(long rows, int cols, const double* __restrict__ src, T* __restrict__ dst, long ldd) {
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; i < count; i += (long)gridDim.x * blockDim.x) dst[i] = (T)src[i];
+  for (; i < rows * cols; i += (long)gridDim.x * blockDim.x) {
+    const long r = i / cols, c = i - r * cols;
+    dst[r * ldd + c] = (T)src[i];
+  }
 }
 
 template <typename T>
@@ -135,16 +192,27 @@ int backtransform(int m, T* L, long ldl, const T* W, long ldw, const T* tau, con
   }
   BSE_LAUNCH_CHECK();
   const int nref = m - 1;  // reflectors j = 0..m-2 act on rows/cols j+1..m-1
+  const long ldv = w.ldv;
   for (int j0 = 0; j0 < nref; j0 += BT_NB) {
     const int nbp = min(BT_NB, nref - j0);
     const int rows = m - j0 - 1;
     {
-      KprofScope ks(K_ELEMENTWISE, s, 2.0 * sizeof(T) * m * BT_NB, 0.0);
-      bt_copy_panel<T><<<dim3(ceil_div(m, 256), BT_NB), 256, 0, s>>>(m, j0, nbp, W, ldw, w.Vb);
+      KprofScope ks(K_ELEMENTWISE, s, 2.0 * sizeof(T) * rows * BT_NB, 0.0);
+      bt_copy_panel<T><<<dim3(ceil_div(ldv, 256), BT_NB), 256, 0, s>>>(m, j0, nbp, W, ldw, w.Vb, ldv);
     }
     BSE_LAUNCH_CHECK();
     // G = V^T V
-    BSE_TRY(gemm<T>(nbp, nbp, rows, 1.0, w.Vb + j0 + 1, m, true, w.Vb + j0 + 1, m, false, 0.0, w.G, BT_NB, s));
+    const int parts = ceil_div(rows, gram_rows<T>());
+    {
+      KprofScope ks(K_ELEMENTWISE, s, sizeof(T) * (double)rows * BT_NB, 2.0 * rows * (double)BT_NB * BT_NB);
+      bt_gram_part<T><<<parts, 256, 0, s>>>(rows, w.Vb, ldv, reinterpret_cast<double*>(w.Gpart));
+    }
+    BSE_LAUNCH_CHECK();
+    {
+      KprofScope ks(K_ELEMENTWISE, s, 8.0 * parts * BT_NB * BT_NB, 0.0);
+      bt_gram_sum<T><<<ceil_div(BT_NB * BT_NB, 256), 256, 0, s>>>(parts, reinterpret_cast<double*>(w.Gpart), w.G);
+    }
+    BSE_LAUNCH_CHECK();
     {
       KprofScope ks(K_ELEMENTWISE, s, 0.0, 0.0);
       bt_larft<T><<<1, BT_NB, 0, s>>>(nbp, w.G, tau + j0, w.Tf);
@@ -152,24 +220,26 @@ int backtransform(int m, T* L, long ldl, const T* W, long ldw, const T* tau, con
     BSE_LAUNCH_CHECK();
     T* Phi = L + (long)(j0 + 1) * ldl;  // columns j0+1..m-1
     // Z = Phi V ; Z2 = Z T ; Phi -= Z2 V^T
-    BSE_TRY(gemm<T>(m, nbp, rows, 1.0, Phi, ldl, false, w.Vb + j0 + 1, m, false, 0.0, w.Z, m, s));
-    BSE_TRY(gemm<T>(m, nbp, nbp, 1.0, w.Z, m, false, w.Tf, BT_NB, false, 0.0, w.Z2, m, s, TRI_NONE, TRI_UPPER));
-    BSE_TRY(gemm<T>(m, rows, nbp, -1.0, w.Z2, m, false, w.Vb + j0 + 1, m, true, 1.0, Phi, ldl, s));
+    BSE_TRY(gemm<T>(m, nbp, rows, 1.0, Phi, ldl, false, w.Vb, ldv, false, 0.0, w.Z, ldv, s));
+    BSE_TRY(gemm<T>(m, nbp, nbp, 1.0, w.Z, ldv, false, w.Tf, BT_NB, false, 0.0, w.Z2, ldv, s, TRI_NONE, TRI_UPPER));
+    BSE_TRY(gemm<T>(m, rows, nbp, -1.0, w.Z2, ldv, false, w.Vb, ldv, true, 1.0, Phi, ldl, s));
   }
   const T* Vsx;
+  long ldvs = n;
   if (sizeof(T) == 4) {
     {
       KprofScope ks(K_ELEMENTWISE, s, 12.0 * m * (double)n, 0.0);
-      to_float_kernel<T><<<1024, 256, 0, s>>>((long)m * n, Vs, w.Vsf);
+      to_float_kernel<T><<<1024, 256, 0, s>>>((long)m, n, Vs, w.Vsf, w.ldvs);
     }
     BSE_LAUNCH_CHECK();
     Vsx = w.Vsf;
+    ldvs = w.ldvs;
   } else {
     Vsx = reinterpret_cast<const T*>(Vs);
   }
   // F_re = Phi[:, even] Vs[even, :],  F_im = Phi[:, odd] Vs[odd, :]
-  BSE_TRY(gemm<T>(m, n, n, 1.0, L, 2 * ldl, false, Vsx, 2L * n, true, 0.0, w.Fre, m, s));
-  BSE_TRY(gemm<T>(m, n, n, 1.0, L + ldl, 2 * ldl, false, Vsx + n, 2L * n, true, 0.0, w.Fim, m, s));
+  BSE_TRY(gemm<T>(m, n, n, 1.0, L, 2 * ldl, false, Vsx, 2L * ldvs, true, 0.0, w.Fre, m, s));
+  BSE_TRY(gemm<T>(m, n, n, 1.0, L + ldl, 2 * ldl, false, Vsx + ldvs, 2L * ldvs, true, 0.0, w.Fim, m, s));
   {
     KprofScope ks(K_ELEMENTWISE, s, 2.0 * sizeof(T) * m * (double)n + 32.0 * m * (double)n, 0.0);
     bt_epilogue<T><<<dim3(ceil_div(n, 128), n), 128, 0, s>>>(n, w.Fre, w.Fim, m, lam, reinterpret_cast<double2*>(X),

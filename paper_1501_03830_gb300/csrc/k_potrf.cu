@@ -83,6 +83,7 @@ size_t potrf_worksize(int m) {
 
 template <typename T>
 int potrf(int m, T* A, long lda, void* work, DevStatus* st, cudaStream_t s) {
+  StatusScope ss(st);
   T* Linv = reinterpret_cast<T*>(work);
   T* Ptmp = Linv + POTRF_NB * POTRF_NB;
   for (int k0 = 0; k0 < m; k0 += POTRF_NB) {

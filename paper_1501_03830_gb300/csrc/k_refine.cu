@@ -537,6 +537,7 @@ static void find_clusters(const std::vector<double>& lam, double tau, std::vecto
 
 int refine(int n, const double* M, double* lam, double* X, int max_sweeps, double tol, void* work, DevStatus* st,
            cudaStream_t s, int* sweeps_done, double* resid, double* dlam_last, double* dlam_first) {
+  StatusScope ss(st);
   const int m = 2 * n;
   RefWork w = carve_ref(work, n);
   const dim3 eg(ceil_div(n, 128), n);

@@ -20,6 +20,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "ptx_sm100.cuh"
 #include "tcgemm.cuh"
 
 namespace bse {
@@ -32,57 +33,11 @@ constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int THREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;  // two 128 x 256 FP32 accumulators
-constexpr long kSpin = 1L << 26;     // bounded waits (~seconds)
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+using namespace ptx;
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait; false (and *err set) on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* err) {
-  for (long it = 0; it < kSpin; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (*err) return false;
-  }
-  *err = BSE_ERR_TIMEOUT;
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
-// groups 1024 bytes apart (rows of 64 bf16 = 128 bytes).
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                   // leading-dimension offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;         // stride-dimension offset: 8 rows x 128 B
-  d |= (uint64_t)1 << 46;                   // descriptor version
-  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
-  return d;
-}
+// K-major operand, rows of 64 bf16 = 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) { return make_desc_sw128(saddr, 16, 1024); }
 
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N = 256, M = 128.
 __host__ __device__ constexpr uint32_t make_idesc() {
@@ -97,26 +52,6 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
       : "memory");
 }
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
-      "[%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcParams P) {
@@ -156,12 +91,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     *err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -171,6 +101,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       // TMA producer
       int it = 0;
+      uint32_t issued = 0, last_par = 0;  // per stage: a load was issued / its phase parity
       for (int u = 0; u < P.units && !*err; ++u) {
         const int ya = P.a_digit[u] * P.a_rows + m0;
         const int yb = P.b_digit[u] * P.b_rows + n0;
@@ -182,8 +113,13 @@ __global__ void __launch_bounds__(THREADS, 1)
           mbar_expect_tx(&full[st], STAGE_BYTES);
           tma_load_2d(sa, &tmA, kb * BK, ya, &full[st]);
           tma_load_2d(sa + A_BYTES, &tmB, kb * BK, yb, &full[st]);
+          issued |= 1u << st;
+          last_par = (last_par & ~(1u << st)) | (ph << st);
         }
       }
+      // the CTA may leave early after an error: first let every issued copy land
+      for (int st = 0; st < STAGES; ++st)
+        if (issued & (1u << st)) mbar_drain(&full[st], (last_par >> st) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -215,8 +151,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       // all issued MMAs complete before TMEM can be released
       umma_commit(drain);
-      for (long w = 0; w < kSpin && !mbar_try_wait(drain, 0); ++w) {
-      }
+      mbar_drain(drain, 0);
     }
   } else {
     // epilogue: TMEM lane quadrant q4 = warp % 4, one output row per thread
@@ -257,12 +192,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+    tmem_dealloc(tmem_base, TMEM_COLS);
   }
   if (threadIdx.x == 0 && *err && P.status) atomicCAS(P.status, 0, *err);
 }
 
 // ---- host side -------------------------------------------------------------
+
+}  // namespace tc
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -281,25 +218,31 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// rows x K bf16, K contiguous with row pitch ldk (elements); box BK x box_rows.
-static int make_map(CUtensorMap* map, const void* base, long rows, long K, long ldk, int box_rows) {
+int make_tensor_map_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, long inner, long outer,
+                       long pitch_bytes, int box_inner, int box_outer) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) {
     record_message("cuTensorMapEncodeTiled is not available");
     return BSE_ERR_CUDA;
   }
-  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ldk * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     record_message("cuTensorMapEncodeTiled failed");
     return BSE_ERR_CUDA;
   }
   return BSE_OK;
+}
+
+namespace tc {
+
+// rows x K bf16, K contiguous with row pitch ldk (elements); box BK x box_rows.
+static int make_map(CUtensorMap* map, const void* base, long rows, long K, long ldk, int box_rows) {
+  return make_tensor_map_2d(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, K, rows, ldk * 2, BK, box_rows);
 }
 
 int tc_gemm(const TcProblem& pb, cudaStream_t s) {

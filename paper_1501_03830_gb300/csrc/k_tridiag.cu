@@ -49,13 +49,15 @@ struct TrdWork {
 constexpr int kMaxGrid = 1024;  // upper bound on the panel kernel's grid
 
 static inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+// VP / PV leading dimension: m rounded up to 32 (aligned panels for the tensor-core update)
+static inline long vp_ld(int m) { return ((long)m + 31) / 32 * 32; }
 
 template <typename T>
 size_t trd_worksize(int m) {
   size_t ns = ceil_div(m, TRD_TB);
   size_t maxQ = ns;  // work items hold >= 1 sub-tile
   size_t b = 0;
-  b += 2 * align256(sizeof(T) * (size_t)m * 2 * TRD_NB);
+  b += 2 * align256(sizeof(T) * (size_t)vp_ld(m) * 2 * TRD_NB);
   b += align256(sizeof(T) * ns * maxQ * TRD_TB);
   b += align256(sizeof(T) * ns * ns * TRD_TB);
   b += align256(sizeof(double) * kMaxGrid);
@@ -70,8 +72,8 @@ static TrdWork<T> carve(void* work, int m) {
   size_t maxQ = ns;
   char* p = reinterpret_cast<char*>(work);
   TrdWork<T> w;
-  w.VP = reinterpret_cast<T*>(p); p += align256(sizeof(T) * (size_t)m * 2 * TRD_NB);
-  w.PV = reinterpret_cast<T*>(p); p += align256(sizeof(T) * (size_t)m * 2 * TRD_NB);
+  w.VP = reinterpret_cast<T*>(p); p += align256(sizeof(T) * (size_t)vp_ld(m) * 2 * TRD_NB);
+  w.PV = reinterpret_cast<T*>(p); p += align256(sizeof(T) * (size_t)vp_ld(m) * 2 * TRD_NB);
   w.Dpart = reinterpret_cast<T*>(p); p += align256(sizeof(T) * ns * maxQ * TRD_TB);
   w.Tpart = reinterpret_cast<T*>(p); p += align256(sizeof(T) * ns * ns * TRD_TB);
   w.normpart = reinterpret_cast<double*>(p); p += align256(sizeof(double) * kMaxGrid);
@@ -102,6 +104,7 @@ struct PanelArgs {
   int m, j0, nbp;
   T* W;
   long ldw;
+  long ldvp;    // leading dimension of VP and PV
   T* VP;
   T* PV;
   T* Dpart;
@@ -380,6 +383,7 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
   T* __restrict__ W = a.W;
   T* VP = a.VP;
   T* PV = a.PV;
+  const long ldvp = a.ldvp;
 
   // phase A for the first panel column: its norm (no pending updates yet)
   {
@@ -429,7 +433,7 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
           T pv = T(0);
           if (q < nq2 && r_own < m) {
             const int col = q < c ? q : TRD_NB + (q - c);
-            pv = ldcg(VP + r_own + (long)col * m) * vr;
+            pv = ldcg(VP + r_own + (long)col * ldvp) * vr;
           }
           acc[k] = pv;
         }
@@ -493,8 +497,8 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
         }
       }
       for (int t = tid; t < c; t += 256) {
-        sVs[t] = ldcg(VP + s + (long)t * m);
-        sPs[t] = ldcg(VP + s + (long)(TRD_NB + t) * m);
+        sVs[t] = ldcg(VP + s + (long)t * ldvp);
+        sPs[t] = ldcg(VP + s + (long)(TRD_NB + t) * ldvp);
       }
       __syncthreads();
       // p at row s (= j+1): every block needs it for the next column's update
@@ -542,7 +546,7 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
         const int j1 = j + 1;
         T w = T(0);
         for (int t = l8; valid && t < c; t += 8) {
-          const T vv = ldcg(VP + r + (long)t * m), pp = ldcg(VP + r + (long)(TRD_NB + t) * m);
+          const T vv = ldcg(VP + r + (long)t * ldvp), pp = ldcg(VP + r + (long)(TRD_NB + t) * ldvp);
           y = fma(vv, sdP[t], y);
           y = fma(-pp, sdV[t], y);
           w = fma(vv, sPs[t], w);
@@ -556,10 +560,10 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
         if (valid && l8 == 0) {
           const T vr = (r == s) ? T(1) : ldcg(W + r + (long)j * ldw) * scal;
           const T p = tauj * y;
-          VP[r + (long)c * m] = vr;
-          VP[r + (long)(TRD_NB + c) * m] = p;
-          PV[r + (long)c * m] = p;
-          PV[r + (long)(TRD_NB + c) * m] = -vr;
+          VP[r + (long)c * ldvp] = vr;
+          VP[r + (long)(TRD_NB + c) * ldvp] = p;
+          PV[r + (long)c * ldvp] = p;
+          PV[r + (long)(TRD_NB + c) * ldvp] = -vr;
           W[r + (long)j * ldw] = vr;  // the reflector, leading 1 included
           if (upd) {
             // column j+1 with all panel terms t <= c; t = c: V[j1, c] = 1, P[j1, c] = p_s
@@ -585,6 +589,7 @@ static int g_trace_cols = 0;
 
 template <typename T>
 int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStream_t st, DevStatus* status) {
+  StatusScope ss(status);
   TrdWork<T> w = carve<T>(work, m);
   BSE_CUDA(cudaMemsetAsync(w.bar, 0, 64, st));
   int dev = 0, nsm = 0, per_sm = 0;
@@ -598,18 +603,19 @@ int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStr
   per_sm = min(per_sm, 2);
   if (nsm * per_sm > kMaxGrid) per_sm = max(1, kMaxGrid / nsm);
   const int ncols = m - 1;  // columns 0..m-2 carry a reflector (the last one is trivial)
+  const long ldvp = vp_ld(m);
   for (int j0 = 0; j0 < ncols; j0 += TRD_NB) {
     const int nbp = min(TRD_NB, ncols - j0);
     // zero rows [j0, m) of the panel buffers
-    BSE_CUDA(cudaMemset2DAsync(w.VP + j0, (size_t)m * sizeof(T), 0, (size_t)(m - j0) * sizeof(T), 2 * TRD_NB, st));
-    BSE_CUDA(cudaMemset2DAsync(w.PV + j0, (size_t)m * sizeof(T), 0, (size_t)(m - j0) * sizeof(T), 2 * TRD_NB, st));
+    BSE_CUDA(cudaMemset2DAsync(w.VP + j0, (size_t)ldvp * sizeof(T), 0, (size_t)(m - j0) * sizeof(T), 2 * TRD_NB, st));
+    BSE_CUDA(cudaMemset2DAsync(w.PV + j0, (size_t)ldvp * sizeof(T), 0, (size_t)(m - j0) * sizeof(T), 2 * TRD_NB, st));
     // enough blocks for the owned rows and the SYMV items, at most per_sm per SM
     const int rows = m - j0 - 1;
     const long sub = (long)ceil_div(rows, TRD_TB);
     const long want = max((long)ceil_div(rows, 256), (sub * (sub + 1) / 2 + 7) / 8);
     const int grid = (int)max(1L, min((long)nsm * per_sm, want));
     PanelArgs<T> pa;
-    pa.m = m; pa.j0 = j0; pa.nbp = nbp; pa.W = W; pa.ldw = ldw; pa.VP = w.VP; pa.PV = w.PV;
+    pa.m = m; pa.j0 = j0; pa.nbp = nbp; pa.W = W; pa.ldw = ldw; pa.VP = w.VP; pa.PV = w.PV; pa.ldvp = ldvp;
     pa.Dpart = w.Dpart; pa.Tpart = w.Tpart; pa.normpart = w.normpart; pa.dotpart = w.dotpart; pa.e = e; pa.tau = tau;
     pa.bar = w.bar; pa.st = status;
     pa.vec = ((ldw * (long)sizeof(T)) % 16 == 0) && ((reinterpret_cast<uintptr_t>(W) % 16) == 0);
@@ -635,7 +641,7 @@ int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStr
     const int N = m - s2;
     if (N > 1 && s2 < ncols) {
       // A0[s2:, s2:] += [V P] [P -V]^T  (strict lower triangle)
-      BSE_TRY(gemm<T>(N, N, 2 * TRD_NB, 1.0, w.VP + s2, m, false, w.PV + s2, m, true, 1.0,
+      BSE_TRY(gemm<T>(N, N, 2 * TRD_NB, 1.0, w.VP + s2, ldvp, false, w.PV + s2, ldvp, true, 1.0,
                       W + s2 + (long)s2 * ldw, ldw, st, TRI_NONE, TRI_NONE, 2));
     }
   }

@@ -105,3 +105,10 @@ extern "C" int bse_kprof_read(int k, long long* launches, double* ms, double* by
   if (flops) *flops = g_flops[k];
   return BSE_OK;
 }
+
+namespace bse {
+DevStatus*& current_status() {
+  static thread_local DevStatus* cur = nullptr;
+  return cur;
+}
+}  // namespace bse

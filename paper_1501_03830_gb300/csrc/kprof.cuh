@@ -25,6 +25,7 @@ enum KClass {
   K_WEIGHTS,
   K_ELEMENTWISE,
   K_GEMM_TC,
+  K_GEMM_TF32,
   K_NUM_CLASSES
 };
 

@@ -53,7 +53,7 @@ size_t workspace_bytes(int n, int precision) {
   size_t b = 0;
   b += 2 * al256(16 * (size_t)n * n);         // A, B staging
   b += al256(8 * m * m);                       // M (FP64)
-  if (f32) b += al256(4 * m * m);              // L (FP32)
+  if (f32) b += al256(4 * w_ld(n) * m);        // L (FP32, leading dimension padded)
   b += al256(ts * w_ld(n) * m);                // W (leading dimension padded)
   b += al256(8 * m) + al256(ts * m) + al256(8 * (size_t)n);  // e, tau, lambda
   b += al256(8 * m * n);                       // Vs
@@ -91,8 +91,8 @@ int Workspace::init(int n_, int precision_) {
   A = (double*)take(16 * (size_t)n * n);
   B = (double*)take(16 * (size_t)n * n);
   M = (double*)take(8 * m * m);
-  Lf = f32 ? (float*)take(4 * m * m) : nullptr;
   ldw = (int)w_ld(n);
+  Lf = f32 ? (float*)take(4 * (size_t)ldw * m) : nullptr;
   W = take(ts * (size_t)ldw * m);
   e = (double*)take(8 * m);
   tau = take(ts * m);
@@ -244,10 +244,11 @@ int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, co
   const int m = 2 * n;
   cudaEvent_t* ev = c->ev;
   const bool tm = c->timing;
+  StatusScope ss(ws->status);
   BSE_CUDA(cudaMemsetAsync(ws->status, 0, sizeof(DevStatus), s));
   if (tm) cudaEventRecord(ev[0], s);
   const bool f32 = precision != BSE_FP64;
-  BSE_TRY(form_M(n, dA, lda, dB, ldb, ws->M, m, f32 ? ws->Lf : nullptr, m, s));
+  BSE_TRY(form_M(n, dA, lda, dB, ldb, ws->M, m, f32 ? ws->Lf : nullptr, ws->ldw, s));
   if (tm) cudaEventRecord(ev[1], s);
   if (!f32) {
     double* W = (double*)ws->W;
@@ -266,16 +267,16 @@ int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, co
   } else {
     float* W = (float*)ws->W;
     float* tau = (float*)ws->tau;
-    BSE_TRY(potrf<float>(m, ws->Lf, m, ws->scratch, ws->status, s));
+    BSE_TRY(potrf<float>(m, ws->Lf, ws->ldw, ws->scratch, ws->status, s));
     if (tm) cudaEventRecord(ev[2], s);
-    BSE_TRY(form_W<float>(n, ws->Lf, m, W, ws->ldw, s));
+    BSE_TRY(form_W<float>(n, ws->Lf, ws->ldw, W, ws->ldw, s));
     if (tm) cudaEventRecord(ev[3], s);
     BSE_TRY(tridiagonalize<float>(m, W, ws->ldw, ws->e, tau, ws->scratch, s, ws->status));
     if (tm) cudaEventRecord(ev[4], s);
     BSE_TRY(tdeig(m, ws->e, ws->lam, ws->Vs, (double*)ws->scratch, ws->status, s));
     if (tm) cudaEventRecord(ev[5], s);
     const bool refine_now = precision == BSE_MIXED_REFINED;
-    BSE_TRY(backtransform<float>(m, ws->Lf, m, W, ws->ldw, tau, ws->Vs, ws->lam, ws->X,
+    BSE_TRY(backtransform<float>(m, ws->Lf, ws->ldw, W, ws->ldw, tau, ws->Vs, ws->lam, ws->X,
                                  (want_Y && !refine_now) ? ws->Y : nullptr, m, ws->scratch, s));
     if (tm) cudaEventRecord(ev[6], s);
     if (refine_now) {

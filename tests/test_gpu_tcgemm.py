@@ -85,3 +85,86 @@ def test_ozaki_fp64_accuracy(M, N, K, s):
     assert np.max(np.abs(got - ref)) <= max(bound, 4e-16 * np.max(scale))
     # FP64-level: far below what FP32 accumulation gives
     assert np.max(np.abs(got - ref) / scale) <= 1e-12
+
+
+# ---- FP32 GEMM on the tensor cores (3xTF32) ---------------------------------
+
+
+def _colmajor(torch, rows, cols, ld, g):
+    """A rows x cols FP32 matrix stored column-major with leading dimension ld,
+    as (storage tensor, the matrix view)."""
+    buf = torch.randn(cols, ld, generator=g, device="cuda", dtype=torch.float32)
+    return buf, buf[:, :rows].t()
+
+
+def _tc32(torch, L, bse, M, N, K, ta, tb, alpha, beta, uplo, split, seed):
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    pad = lambda x: (x + 3) // 4 * 4 + 4
+    ar, ac = (K, M) if ta else (M, K)
+    br, bc = (N, K) if tb else (K, N)
+    Abuf, A = _colmajor(torch, ar, ac, pad(ar), g)
+    Bbuf, B = _colmajor(torch, br, bc, pad(br), g)
+    Cbuf, Cm = _colmajor(torch, M, N, M + 1, g)
+    C0 = Cm.double().clone()
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")
+    bse.check(L.bse_tc32_gemm(M, N, K, alpha, Abuf.data_ptr(), Abuf.shape[1], int(ta), Bbuf.data_ptr(),
+                              Bbuf.shape[1], int(tb), beta, Cbuf.data_ptr(), M + 1, uplo, split, st.data_ptr(), None),
+              "tc32")
+    torch.cuda.synchronize()
+    assert int(st[0].item()) == 0
+    opA = A.double().t() if ta else A.double()
+    opB = B.double().t() if tb else B.double()
+    ref = alpha * (opA @ opB) + beta * C0
+    scale = abs(alpha) * (opA.abs() @ opB.abs())
+    return Cm.double(), ref, scale, C0
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 0), (0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("M,N,K", [(128, 128, 32), (300, 200, 150), (257, 131, 77), (1000, 700, 600)])
+def test_tc32_gemm_3xtf32(ta, tb, M, N, K):
+    """3xTF32 reaches FP32-level accuracy for every transpose combination, with
+    ragged tiles in M, N and K (bound: a few units of 2^-21 times |A||B|)."""
+    torch = torch_cuda()
+    L, bse = _lib()
+    C, ref, scale, _ = _tc32(torch, L, bse, M, N, K, ta, tb, -1.5, 0.5, 0, 1, 11 + M + 2 * ta + tb)
+    err = ((C - ref).abs() / (scale + 1e-30)).max().item()
+    assert err < 4e-6, err
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 0), (1, 0)])
+def test_tc32_gemm_single_pass(ta, tb):
+    """One TF32 pass: 10-bit operands, so errors of order 2^-11 |A||B| and clearly
+    above those of the 3xTF32 path on the same inputs."""
+    torch = torch_cuda()
+    L, bse = _lib()
+    C1, ref, scale, _ = _tc32(torch, L, bse, 384, 256, 512, ta, tb, 1.0, 0.0, 0, 0, 5)
+    C3, _, _, _ = _tc32(torch, L, bse, 384, 256, 512, ta, tb, 1.0, 0.0, 0, 1, 5)
+    e1 = ((C1 - ref).abs() / scale).max().item()
+    e3 = ((C3 - ref).abs() / scale).max().item()
+    assert e1 < 2e-3 and e3 < 4e-6 and e1 > 20 * e3, (e1, e3)
+
+
+@pytest.mark.parametrize("uplo", [1, 2])
+def test_tc32_gemm_lower_triangle(uplo):
+    """uplo = 1 / 2: the lower (strict lower) triangle is the product, the rest of C is untouched."""
+    torch = torch_cuda()
+    L, bse = _lib()
+    n = 600
+    C, ref, scale, C0 = _tc32(torch, L, bse, n, n, 128, 0, 1, 1.0, 1.0, uplo, 1, 21 + uplo)
+    i = torch.arange(n, device="cuda")
+    low = (i[:, None] >= i[None, :]) if uplo == 1 else (i[:, None] > i[None, :])
+    assert torch.equal(C[~low], C0[~low])
+    err = ((C - ref).abs() / scale)[low].max().item()
+    assert err < 4e-6, err
+
+
+def test_tc32_gemm_rejects_unaligned_pitch():
+    torch = torch_cuda()
+    L, bse = _lib()
+    A = torch.zeros(64 * 65, device="cuda")
+    C = torch.zeros(64 * 64, device="cuda")
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")
+    rc = L.bse_tc32_gemm(64, 64, 64, 1.0, A.data_ptr(), 65, 0, A.data_ptr(), 65, 0, 0.0, C.data_ptr(), 64, 0, 1,
+                         st.data_ptr(), None)
+    assert rc == -1

@@ -378,6 +378,15 @@ def roofline(kp: dict, peaks: dict, torch, device) -> dict:
                 "frac": achieved / peak, "traffic": None, "launches": st["launches"],
                 "avg_launch_ms": st["ms"] / max(1, st["launches"]),
                 "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({peaks['_source']})"}
+    if name == "gemm_tf32":
+        # 3xTF32: three TF32 tensor passes per FP32 product; TF32 peak = measured bf16 x 1.1/2.25 (nominal ratio)
+        achieved = st["flops"] / sec / 1e12
+        peak = float(peaks.get("bf16_tflops")) * (1.1 / 2.25) / 3.0
+        return {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "launches": st["launches"],
+                "avg_launch_ms": st["ms"] / max(1, st["launches"]),
+                "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({peaks['_source']}) x 1.1/2.25 (TF32) / 3 "
+                               "(3xTF32 passes per FP32 flop)"}
     # SIMT GEMMs: bound by the FP64 or FP32 ALUs; the peak is cuBLAS of the same dtype measured here
     dt = torch.float64 if name == "gemm_f64" else torch.float32
     achieved = st["flops"] / sec / 1e12

@@ -1,0 +1,112 @@
+"""Time one kernel family of the solver in isolation, on synthetic device data.
+
+    python -m paper_1501_03830_gb300.stagebench tc32 --M 4096 --N 4096 --K 4096
+    python -m paper_1501_03830_gb300.stagebench ozaki --M 4096 --N 4096 --K 16384 --s 10
+    python -m paper_1501_03830_gb300.stagebench tridiag --m 8192 [--fp64]
+    python -m paper_1501_03830_gb300.stagebench tdeig --m 16384
+
+Each run does --reps launches (CUDA events on the launch stream, after one
+warm-up launch) and prints one line with the mean time and the achieved rate
+charged with the algorithmic flops or bytes of the stage. It is the command the
+kernel profiles are taken with (ncu -k <kernel> on the same command line).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+from . import bse
+
+
+def _timed(torch, fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run(argv=None) -> dict:
+    import torch
+
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("stage", choices=["tc32", "ozaki", "tridiag", "tdeig"])
+    ap.add_argument("--M", type=int, default=4096)
+    ap.add_argument("--N", type=int, default=4096)
+    ap.add_argument("--K", type=int, default=4096)
+    ap.add_argument("--s", type=int, default=10, help="digits per operand (ozaki)")
+    ap.add_argument("--split", type=int, default=1, help="tc32: 1 = 3xTF32, 0 = one TF32 pass")
+    ap.add_argument("--m", type=int, default=8192, help="matrix order (tridiag, tdeig)")
+    ap.add_argument("--fp64", action="store_true", help="tridiag in FP64 instead of FP32")
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args(argv)
+    L = bse.lib()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1)
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")
+    out = {"stage": a.stage}
+    if a.stage == "tc32":
+        A = torch.randn(a.K, a.M, generator=g, device="cuda")  # column-major M x K, ld M
+        B = torch.randn(a.N, a.K, generator=g, device="cuda")  # column-major K x N, ld K
+        C = torch.zeros(a.N, a.M, device="cuda")
+        fn = lambda: bse.check(L.bse_tc32_gemm(a.M, a.N, a.K, 1.0, A.data_ptr(), a.M, 0, B.data_ptr(), a.K, 0, 0.0,
+                                                 C.data_ptr(), a.M, 0, a.split, st.data_ptr(), None), "tc32")
+        ms = _timed(torch, fn, a.reps)
+        out.update(M=a.M, N=a.N, K=a.K, split=a.split, ms=ms, tflops=2.0 * a.M * a.N * a.K / ms / 1e9)
+    elif a.stage == "ozaki":
+        A = torch.randn(a.M, a.K, dtype=torch.float64, device="cuda", generator=g)
+        B = torch.randn(a.N, a.K, dtype=torch.float64, device="cuda", generator=g)
+        C = torch.zeros(a.N, a.M, dtype=torch.float64, device="cuda")
+        work = torch.empty(L.bse_ozaki_worksize(a.M, a.N, a.K, a.s), dtype=torch.uint8, device="cuda")
+        fn = lambda: bse.check(L.bse_ozaki_gemm(a.M, a.N, a.K, A.data_ptr(), a.K, B.data_ptr(), a.K, C.data_ptr(), a.M,
+                                                a.s, work.data_ptr(), st.data_ptr(), None), "ozaki")
+        ms = _timed(torch, fn, a.reps)
+        units = a.s * (a.s + 1) // 2
+        out.update(M=a.M, N=a.N, K=a.K, s=a.s, units=units, ms=ms,
+                   fp64_tflops=2.0 * a.M * a.N * a.K / ms / 1e9,
+                   bf16_tflops=2.0 * a.M * a.N * a.K * units / ms / 1e9)
+    elif a.stage == "tridiag":
+        fp32 = 0 if a.fp64 else 1
+        dt = torch.float32 if fp32 else torch.float64
+        m = a.m
+        W0 = torch.tril(torch.randn(m, m, dtype=dt, device="cuda", generator=g), -1)
+        Wm = torch.empty_like(W0)
+        e = torch.empty(m, dtype=torch.float64, device="cuda")
+        tau = torch.empty(m, dtype=dt, device="cuda")
+        work = torch.empty(L.bse_stage_tridiag_worksize(m, fp32), dtype=torch.uint8, device="cuda")
+
+        def fn():
+            Wm.copy_(W0)
+            bse.check(L.bse_stage_tridiag(m, Wm.data_ptr(), m, e.data_ptr(), tau.data_ptr(), fp32, work.data_ptr(),
+                                          st.data_ptr(), None), "tridiag")
+
+        ms = _timed(torch, fn, a.reps)
+        esz = 4 if fp32 else 8
+        out.update(m=m, fp32=fp32, ms=ms, symv_bytes=esz * m ** 3 / 6.0)
+    else:
+        m = a.m
+        e = torch.rand(m, dtype=torch.float64, device="cuda", generator=g) + 0.5
+        lam = torch.empty(m // 2, dtype=torch.float64, device="cuda")
+        Vs = torch.empty(m * (m // 2), dtype=torch.float64, device="cuda")
+        work = torch.empty(L.bse_stage_tdeig_worksize(m), dtype=torch.uint8, device="cuda")
+        fn = lambda: bse.check(L.bse_stage_tdeig(m, e.data_ptr(), lam.data_ptr(), Vs.data_ptr(), work.data_ptr(),
+                                                 st.data_ptr(), None), "tdeig")
+        ms = _timed(torch, fn, a.reps)
+        out.update(m=m, ms=ms)
+    torch.cuda.synchronize()
+    out["status"] = int(st[0].item())
+    if out["status"] != 0:
+        raise bse.BSEError(out["status"], a.stage, "device status")
+    return out
+
+
+def main(argv=None) -> None:
+    print(json.dumps(run(argv)))
+
+
+if __name__ == "__main__":
+    main()

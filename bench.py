@@ -43,6 +43,13 @@ def parse():
     ap.add_argument("--cpu-n", type=int, default=1280, help="oracle sample size for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=8192)
+    ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single",
+                    help="single: one problem of size --n per step (default); batched: 512 problems, n log-uniform "
+                         "in [32, 512] per step; serving: the Poisson request stream")
+    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--check", type=int, default=24, help="problems checked against the oracle (batched/serving)")
+    ap.add_argument("--requests", type=int, default=400)
+    ap.add_argument("--slots", type=int, default=0, help="streams for batched/serving (0: library default)")
     return ap.parse_args()
 
 
@@ -416,10 +423,231 @@ def cublas_peak(torch, dtype, device, N=8192, it=3) -> float:
     return 2.0 * N ** 3 * it / (e0.elapsed_time(e1) * 1e-3) / 1e12
 
 
+# --- batched workload ------------------------------------------------------------
+
+def run_batched(args):
+    """512 independent problems, n log-uniform in [32, 512]; one step = one
+    bse_solve_batched call over all of them with inputs and outputs in HBM."""
+    import numpy as np
+    import torch
+
+    from oracle import definition as D
+    from paper_1501_03830_gb300 import bse
+    from paper_1501_03830_gb300.synth import batch_sizes, make_problem
+
+    ws, rank, local = dist_env()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if args.slots:
+        os.environ["BSE_BATCH_SLOTS"] = str(args.slots)
+    ns = [int(v) for v in batch_sizes(args.batch, 32, 512, seed=args.seed + rank)]
+    probs = [make_problem(n, args.seed + 1000 * rank + i) for i, n in enumerate(ns)]
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1 and rank == 0:
+        # the oracle on a bounded sample of the batch: the first problems until ~10 s
+        t0 = time.perf_counter()
+        done = 0
+        for p in probs:
+            D.solve(p.A, p.B)
+            done += 1
+            if time.perf_counter() - t0 > 10.0:
+                break
+        dt = time.perf_counter() - t0
+        sample_n3 = sum(pp.n ** 3 for pp in probs[:done])
+        all_n3 = sum(pp.n ** 3 for pp in probs)
+        cpu = {"value": len(probs) / (dt * all_n3 / sample_n3), "unit": "solves/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"oracle on the first {done} problems of the batch ({dt:.1f} s), scaled to the whole "
+                         "batch by sum n^3"}
+    dev = [(to_dev_colmajor(torch, p.A, device), to_dev_colmajor(torch, p.B, device)) for p in probs]
+    outs = [(torch.empty(p.n, dtype=torch.float64, device=device),
+             torch.empty(2 * p.n * p.n, dtype=torch.complex128, device=device)) for p in probs]
+    ctx = bse.Context(local)
+    stream = torch.cuda.Stream(device)
+    ctx.set_stream(stream.cuda_stream)
+
+    def step():
+        _, st = ctx.solve_batched(dev, precision=args.precision, outs=outs)
+        if np.any(st != 0):
+            raise RuntimeError(f"batched solve failed: statuses {sorted(set(st.tolist()))}")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(device)
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = bse.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    launches = bse.launch_count() - launches0
+    clocks = sampler.stop()
+    t_ms = e0.elapsed_time(e1)
+    value = len(probs) * args.steps / (t_ms * 1e-3)
+    # per-problem parity against the oracle on a spread of sizes
+    order = np.argsort(ns)
+    pick = sorted(set(order[np.linspace(0, len(ns) - 1, min(args.check, len(ns))).astype(int)].tolist()))
+    worst_eig, worst_res = 0.0, 0.0
+    for i in pick:
+        p = probs[i]
+        lam = outs[i][0].cpu().numpy()
+        X = np.asfortranarray(outs[i][1].cpu().numpy().reshape(p.n, 2 * p.n).T)
+        ref = D.solve(p.A, p.B)
+        worst_eig = max(worst_eig, float(np.max(np.abs(lam - ref.lam) / np.abs(ref.lam))))
+        worst_res = max(worst_res, float(np.max(D.scaled_residuals(p.A, p.B, lam, X)) / (p.n * 2.0 ** -52)))
+    out = {
+        "metric": "batched BSE solves/s (512 problems, n log-uniform [32, 512], mixed+refined)",
+        "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{len(probs)} independent BSE solves per step, n log-uniform in [32, 512] "
+                               f"(sum n^3 = {sum(n ** 3 for n in ns):.3g}), {args.precision}, all in HBM",
+                   "slots": int(os.environ.get("BSE_BATCH_SLOTS", "8")),
+                   "l2": "inputs + outputs of one step ~" + f"{sum(48 * n * n for n in ns) / 1e6:.0f} MB, "
+                         "larger than L2"},
+        "accuracy": {"checked_problems": len(pick), "max_rel_eig_err_vs_oracle": worst_eig,
+                     "max_scaled_residual_over_n_eps": worst_res},
+        "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks,
+    }
+    print(json.dumps(out))
+    ctx.close()
+    return 0
+
+
+# --- serving workload ------------------------------------------------------------
+
+def serving_stream(count: int, seed: int, pool: int = 96):
+    """Request sizes: n log-uniform in [64, 4096], except 5% at n = 8192. To bound
+    host memory the requests draw from a pool of `pool` distinct seeded problems
+    (plus one at n = 8192); every request is solved from scratch."""
+    import numpy as np
+
+    from paper_1501_03830_gb300.synth import batch_sizes
+
+    rng = np.random.default_rng(seed)
+    pool_n = [int(v) for v in batch_sizes(pool, 64, 4096, seed=seed + 1)]
+    big = set(rng.choice(count, size=max(1, round(0.05 * count)), replace=False).tolist())
+    picks = [(-1 if i in big else int(rng.integers(pool))) for i in range(count)]
+    return pool_n, picks
+
+
+def run_serving(args):
+    """Poisson stream of `--requests` solves through bse_submit / bse_poll with host
+    buffers: first a burst (every request at t = 0) to measure the capacity, then
+    arrivals at 0.8 x that capacity; p50 / p99 latency = completion - arrival."""
+    import numpy as np
+    import torch
+
+    from oracle import definition as D
+    from paper_1501_03830_gb300 import bse
+    from paper_1501_03830_gb300.synth import make_problem, poisson_arrivals
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pool_n, picks = serving_stream(args.requests, args.seed)
+    pool = [make_problem(n, args.seed + 10 + k) for k, n in enumerate(pool_n)]
+    big = make_problem(8192, args.seed + 9)
+    probs = [big if k < 0 else pool[k] for k in picks]
+    slots = args.slots or 4
+    ctx = bse.Context(local)
+    # warm every kernel once (a small and a large size)
+    for q in (pool[int(np.argmin(pool_n))], pool[int(np.argmax(pool_n))]):
+        ctx.solve(q.A, q.B, precision=args.precision)
+    # result buffers per distinct problem: requests of the same problem write the same bits
+    bufs = {}
+    for p in probs:
+        if id(p) not in bufs:
+            bufs[id(p)] = (np.empty(p.n), np.empty((2 * p.n, p.n), dtype=np.complex128, order="F"))
+    outs = [bufs[id(p)] for p in probs]
+
+    def run_stream(arrivals, precision):
+        ctx.serve_start(slots)
+        reqs = [bse.make_request(p.n, p.A, p.B, o[0], o[1], precision=precision) for p, o in zip(probs, outs)]
+        tickets = [None] * len(probs)
+        done = {}
+        t0 = time.perf_counter()
+        nxt = 0
+        while len(done) < len(probs):
+            now = time.perf_counter() - t0
+            while nxt < len(probs) and arrivals[nxt] <= now:
+                tickets[nxt] = ctx.submit(reqs[nxt])
+                nxt += 1
+            for i in range(nxt):
+                if i not in done:
+                    ok, res = ctx.poll(tickets[i])
+                    if ok:
+                        done[i] = (time.perf_counter() - t0, res.status)
+            time.sleep(0.0005)
+        total = time.perf_counter() - t0
+        assert ctx.serve_stop(60.0) == 0
+        bad = [i for i, (_, st) in done.items() if st != 0]
+        if bad:
+            raise RuntimeError(f"{len(bad)} requests failed")
+        lat = np.array([done[i][0] - arrivals[i] for i in range(len(probs))])
+        return total, lat
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = bse.launch_count()
+    t_burst, lat_burst = run_stream(np.zeros(len(probs)), args.precision)
+    capacity = len(probs) / t_burst
+    rate = 0.8 * capacity
+    arrivals = poisson_arrivals(len(probs), rate, seed=args.seed + 2)
+    arrivals -= arrivals[0]
+    t_pois, lat = run_stream(arrivals, args.precision)
+    launches = bse.launch_count() - launches0
+    clocks = sampler.stop()
+    fp64 = None
+    if args.fp64_steps > 0 and args.precision != "fp64":
+        t64, lat64 = run_stream(np.zeros(len(probs)), "fp64")
+        fp64 = {"capacity_solves_per_s": len(probs) / t64, "burst_p50_s": float(np.percentile(lat64, 50)),
+                "burst_p99_s": float(np.percentile(lat64, 99))}
+    # parity of a spread of requests against the oracle (sizes <= 1024 keep it quick)
+    small = [i for i, p in enumerate(probs) if p.n <= 1024]
+    check = sorted(set(small[k] for k in np.linspace(0, len(small) - 1, min(args.check, len(small))).astype(int)))
+    worst = 0.0
+    refs = {}
+    for i in check:
+        p = probs[i]
+        if id(p) not in refs:
+            refs[id(p)] = D.solve(p.A, p.B).lam
+        worst = max(worst, float(np.max(np.abs(outs[i][0] - refs[id(p)]) / np.abs(refs[id(p)]))))
+    ns = [p.n for p in probs]
+    out = {
+        "metric": "serving: BSE solves/s and p50/p99 latency (Poisson stream, mixed+refined)",
+        "value": len(probs) / t_pois, "unit": UNIT, "n_gpus": ws, "steps": 1, "warmup": 1,
+        "ms_per_step": t_pois * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{len(probs)} requests, n log-uniform in [64, 4096] with "
+                               f"{sum(1 for k in picks if k < 0)} at n = 8192, Poisson arrivals at 0.8 x measured "
+                               f"capacity ({rate:.3f} req/s), host buffers, {slots} slots",
+                   "pool": f"{len(pool)} distinct seeded problems + 1 at n = 8192",
+                   "sum_n3": float(sum(float(n) ** 3 for n in ns))},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "max": float(lat.max())},
+        "capacity_solves_per_s": capacity,
+        "burst_latency_s": {"p50": float(np.percentile(lat_burst, 50)), "p99": float(np.percentile(lat_burst, 99))},
+        "fp64_path": fp64,
+        "accuracy": {"checked_requests": len(check), "max_rel_eig_err_vs_oracle": worst},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    print(json.dumps(out))
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

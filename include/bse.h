@@ -166,9 +166,13 @@ int bse_serve_stop(bse_ctx* ctx, double timeout_s);
 /* ---- batched solves ----------------------------------------------------- */
 /* Solve `count` independent problems of sizes ns[i] in one call. A[i], B[i]
  * are host or device pointers (ld = ns[i]); lambdas[i] (ns[i] doubles) and
- * Xs[i] (2ns[i] x ns[i] complex128, nullable) receive the results. Problems
- * are grouped by size and run as batched launches; per-problem status goes to
- * statuses[i] (nullable). */
+ * Xs[i] (2ns[i] x ns[i] complex128, nullable) receive the results. The
+ * problems are dealt largest first to several streams of the context's GPU
+ * (8 by default; BSE_BATCH_SLOTS overrides, 1..32), each with its own workspace
+ * cache, so their pipelines overlap on the device; every problem runs the
+ * kernels of a single bse_solve and gets bit-for-bit its results. Per-problem
+ * status goes to statuses[i] (nullable); the return value is the first
+ * failure, or BSE_OK. Blocks until every result is in place. */
 int bse_solve_batched(bse_ctx* ctx, int count, const int* ns, const double* const* A,
                       const double* const* B, int precision, double* const* lambdas,
                       double* const* Xs, int* statuses);

@@ -261,6 +261,41 @@ class Context:
         check(lib().bse_spectrum(self.handle, sol.handle, ptr(d_r), ptr(d_l), ptr(w)), "bse_spectrum")
         return w
 
+    def solve_batched(self, problems, precision="mixed_refined", want_X=True, outs=None):
+        """bse_solve_batched over a list of (A, B) pairs (numpy host arrays or
+        device tensors, each n x n complex128). Results go to ``outs`` (a list of
+        (lambda, X) buffers, X may be None) or to new host arrays. Returns
+        (list of (lambda, X), per-problem status array)."""
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        count = len(problems)
+        keep = []  # holds the marshalled inputs alive for the call
+        ns = (C.c_int * count)()
+        pa = (C.c_void_p * count)()
+        pb = (C.c_void_p * count)()
+        pl = (C.c_void_p * count)()
+        px = (C.c_void_p * count)()
+        results = []
+        for i, (A, B) in enumerate(problems):
+            if isinstance(A, np.ndarray):
+                A = _fortran_c128(A)
+                B = _fortran_c128(B)
+                n = A.shape[0]
+            else:
+                n = A.shape[-1]
+            keep.append((A, B))
+            if outs is not None:
+                lam, X = outs[i]
+            else:
+                lam = np.empty(n, dtype=np.float64)
+                X = np.empty((2 * n, n), dtype=np.complex128, order="F") if want_X else None
+            results.append((lam, X))
+            ns[i], pa[i], pb[i], pl[i], px[i] = n, ptr(A), ptr(B), ptr(lam), ptr(X)
+        st = (C.c_int * count)()
+        rc = lib().bse_solve_batched(self.handle, count, ns, pa, pb, prec, pl, px, st)
+        if rc != 0 and not any(st):  # a call-level failure (per-problem ones are in the statuses)
+            check(rc, "bse_solve_batched")
+        return results, np.array(list(st), dtype=np.int32)
+
     # --- request loop ---------------------------------------------------------
     def serve_start(self, slots: int = 2) -> None:
         check(lib().bse_serve_start(self.handle, slots), "bse_serve_start")
@@ -286,8 +321,18 @@ class Context:
 
 
 def make_request(n, A, B, lam, X=None, d_r=None, d_l=None, w=None, precision="mixed_refined") -> bse_request:
+    """A request for bse_submit. numpy inputs are laid out column-major here; the
+    request keeps references to every buffer it points to, so they live as long
+    as the request object (keep it until bse_poll reports it done)."""
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    if isinstance(A, np.ndarray):
+        A = _fortran_c128(A)
+        B = _fortran_c128(B)
+    if isinstance(d_r, np.ndarray):
+        d_r = np.ascontiguousarray(d_r, dtype=np.complex128)
+        d_l = np.ascontiguousarray(d_l, dtype=np.complex128)
     r = bse_request()
+    r._keep = (A, B, lam, X, d_r, d_l, w)
     r.n = n
     r.A, r.B = ptr(A), ptr(B)
     r.d_r, r.d_l = ptr(d_r), ptr(d_l)

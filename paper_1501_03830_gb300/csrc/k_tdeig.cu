@@ -5,11 +5,10 @@
 // tridiagonal with zero diagonal and off-diagonal alpha_k = -beta_k (remark 2).
 // Its eigenvalues come in +/- pairs; the positive ones are lambda_1..lambda_n.
 //
-// Eigenvalues: bisection on the Sturm count of Tsym - sigma I (LDL^T pivots
-// d_0 = -sigma, d_k = -sigma - alpha_{k-1}^2 / d_{k-1}), one thread per
-// eigenvalue (the bisection of PDSTEBZ in the paper's implementation). For a
-// zero-diagonal tridiagonal this determines every eigenvalue to high relative
-// accuracy; iteration stops at a relative interval width of 2 eps.
+// Eigenvalues: bisection on the Sturm count of Tsym - sigma I (the number of
+// sign changes among its leading principal minors), as PDSTEBZ does in the
+// paper's implementation, here as multisection with a group of lanes per
+// eigenvalue; iteration stops at a relative interval width of 2 eps.
 //
 // Eigenvectors: a twisted factorization per eigenvalue (forward and backward
 // stationary LDL^T sweeps, twist index r = argmin |gamma_r|, then the two
@@ -61,35 +60,98 @@ __global__ void __launch_bounds__(1024) tdeig_prep(int m, const double* __restri
   }
 }
 
-__device__ __forceinline__ int sturm_count(int m, const double* __restrict__ e2, double sigma, double pivmin) {
-  double q = -sigma;
-  if (fabs(q) < pivmin) q = -pivmin;
-  int c = q < 0.0;
-  for (int k = 1; k < m; ++k) {
-    q = -sigma - e2[k - 1] / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    c += q < 0.0;
+// Number of eigenvalues of Tsym below sigma: sign changes of the leading
+// principal minors p_k = det(T_k - sigma I), p_0 = 1, p_1 = -sigma,
+// p_k = -sigma p_{k-1} - alpha_{k-2}^2 p_{k-2}. The product -alpha^2 p_{k-2} is
+// ready one step early, so each step has a single FP64 FMA on its dependent
+// path (FP64 latency is long on this GPU; an FP64 division, as in the ratio form
+// p_k / p_{k-1}, is ~20x longer still); the sign tests run on the integer pipe
+// from the bit patterns. A minor that vanishes exactly is replaced by
+// -2^-600 p_{k-1} (the ratio form's guard for a zero pivot: the ratio is taken
+// as tiny and negative). Every 8 steps the pair
+// (p_{k-1}, p_k) is rescaled by an exact power of two when it drifts out of
+// [2^-480, 2^480], which changes no sign.
+__device__ __forceinline__ void sturm_step(double ns, double e2k, double& p0, double& p1, int& c) {
+  const double t = -e2k * p0;  // off the dependent path
+  double p2 = fma(ns, p1, t);
+  if ((__double_as_longlong(p2) << 1) == 0) p2 = -0x1p-600 * p1;  // exact zero minor (rare)
+  c += (__double_as_longlong(p2) ^ __double_as_longlong(p1)) < 0;
+  p0 = p1;
+  p1 = p2;
+}
+
+__device__ __forceinline__ void sturm_rescale(double& p0, double& p1) {
+  const int x0 = (int)((__double_as_longlong(p0) >> 52) & 0x7ff);
+  const int x1 = (int)((__double_as_longlong(p1) >> 52) & 0x7ff);
+  const int x = max(x0, x1);
+  if (x > 1023 + 480) {
+    p0 *= 0x1p-480;
+    p1 *= 0x1p-480;
+  } else if (x < 1023 - 480) {
+    p0 *= 0x1p480;
+    p1 *= 0x1p480;
   }
+}
+
+__device__ __forceinline__ int sturm_count(int m, const double* __restrict__ e2, double sigma, double pivmin) {
+  const double ns = -sigma;
+  double p0 = 1.0;  // p_{k-1}
+  double p1 = ns;   // p_k
+  if (fabs(p1) < pivmin) p1 = -pivmin;
+  int c = p1 < 0.0;
+  int k = 1;
+  for (; k + 8 <= m; k += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) sturm_step(ns, e2[k - 1 + u], p0, p1, c);
+    sturm_rescale(p0, p1);
+  }
+  for (; k < m; ++k) sturm_step(ns, e2[k - 1], p0, p1, c);
   return c;
 }
 
-__global__ void __launch_bounds__(32) tdeig_bisect(int m, int n, const double* __restrict__ e2,
+// Multisection: a group of L lanes brackets one eigenvalue; each round the
+// lanes count at L interior points splitting [lo, hi] into L+1 parts, and the
+// part holding eigenvalue number g (the first point whose count exceeds g)
+// becomes the new bracket: log2(L+1) bits per round instead of one, with L
+// independent Sturm chains in flight to hide the FP64 latency. Every lane of
+// a group takes the same decision from the group's ballot, so the bracket
+// stays identical across the group without a broadcast. The loop ends at a
+// relative width of 2 eps (or when the points can no longer split it).
+template <int L>
+__global__ void __launch_bounds__(256) tdeig_msect(int m, int n, const double* __restrict__ e2,
                                                    const double* __restrict__ scal, double* __restrict__ lam,
                                                    DevStatus* st) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const int g = n + j;  // ascending index among all m eigenvalues
+  static_assert(L == 4 || L == 8 || L == 16 || L == 32, "group size");
+  const int lane = threadIdx.x & 31;
+  const int gl = lane % L;       // lane within the group
+  const int gshift = lane - gl;  // first lane of the group in the warp
+  const int j = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) / L);
   const double pivmin = scal[1];
+  const int g = n + j;  // ascending index among all m eigenvalues
   double lo = 0.0, hi = scal[0];
-  int it = 0;
-  for (; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) || mid <= lo || mid >= hi) break;
-    if (sturm_count(m, e2, mid, pivmin) > g) hi = mid;
-    else lo = mid;
+  bool done = j >= n;
+  int rounds = 0;
+  while (!__all_sync(0xffffffffu, done)) {
+    const double h = (hi - lo) / (double)(L + 1);
+    const double sigma = lo + (double)(gl + 1) * h;
+    const int c = done ? 0 : sturm_count(m, e2, sigma, pivmin);
+    const unsigned above = __ballot_sync(0xffffffffu, !done && c > g);
+    const unsigned mask = (L == 32) ? above : ((above >> gshift) & ((1u << L) - 1u));
+    if (!done) {
+      // first point whose count exceeds g: the eigenvalue lies just below it
+      const int first = mask ? __ffs(mask) - 1 : L;
+      const double nlo = first == 0 ? lo : lo + (double)first * h;
+      const double nhi = first == L ? hi : lo + (double)(first + 1) * h;
+      lo = nlo;
+      hi = fmax(nhi, nlo);
+      if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) || h <= 0.0) done = true;
+      if (++rounds >= 128 && !done) {
+        set_status(st, BSE_ERR_NOT_CONVERGED, j + 1);
+        done = true;
+      }
+    }
   }
-  if (it >= 200) set_status(st, BSE_ERR_NOT_CONVERGED, j + 1);
-  lam[j] = 0.5 * (lo + hi);
+  if (j < n && gl == 0) lam[j] = 0.5 * (lo + hi);
 }
 
 __global__ void __launch_bounds__(32) tdeig_vectors(int m, int n, const double* __restrict__ e,
@@ -178,8 +240,15 @@ int tdeig(int m, const double* e, double* lam, double* Vs, double* work, DevStat
   }
   BSE_LAUNCH_CHECK();
   {
+    // lanes per eigenvalue: enough independent Sturm chains to cover the GPU,
+    // few enough not to waste FP64 throughput on large problems
     KprofScope ks(K_TDEIG_BISECT, s, 0.0, 0.0);
-    tdeig_bisect<<<ceil_div(n, 32), 32, 0, s>>>(m, n, e2, scal, lam, st);
+    if (n >= 4096)
+      tdeig_msect<8><<<ceil_div((long)n * 8, 256), 256, 0, s>>>(m, n, e2, scal, lam, st);
+    else if (n >= 1024)
+      tdeig_msect<16><<<ceil_div((long)n * 16, 256), 256, 0, s>>>(m, n, e2, scal, lam, st);
+    else
+      tdeig_msect<32><<<ceil_div((long)n * 32, 256), 256, 0, s>>>(m, n, e2, scal, lam, st);
   }
   BSE_LAUNCH_CHECK();
   if (Vs) {

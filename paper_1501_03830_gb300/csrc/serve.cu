@@ -9,7 +9,10 @@
 // (it is admitted first once it fits). Device-resident state (A, B, M, L, the
 // reflectors, X) stays in the slot's workspace for the whole request; only the
 // requested results are copied back.
+#include <algorithm>
 #include <atomic>
+#include <cstdlib>
+#include <string>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -92,8 +95,8 @@ static void worker_main(ServeState* S, bse_ctx* c) {
     while (c->ws.size() > 1) {
       auto victim = c->ws.begin();
       for (auto i = c->ws.begin(); i != c->ws.end(); ++i)
-        if (i->second.last_use < victim->second.last_use) victim = i;
-      victim->second.release();
+        if (i->last_use < victim->last_use) victim = i;
+      victim->release();
       c->ws.erase(victim);
     }
     res.status = rc;
@@ -209,16 +212,72 @@ extern "C" int bse_serve_stop(bse_ctx* c, double timeout_s) {
   return drained ? BSE_OK : BSE_ERR_TIMEOUT;
 }
 
+// Batched solves: the problems are dealt, largest first, to `slots` host
+// threads, each driving its own context (stream + workspace cache) on the GPU,
+// so the pipelines of different problems overlap on the device while each one
+// runs exactly the kernels (and gives exactly the results) of a single
+// bse_solve. Largest-first dealing keeps the slots' finishing times close and
+// lets each slot's first workspace (sized for its largest problem) serve all of
+// its later, smaller problems without new allocations.
+static int batch_slots_for(bse_ctx* c, int count) {
+  const char* env = getenv("BSE_BATCH_SLOTS");
+  int slots = env ? atoi(env) : 8;
+  if (slots < 1) slots = 1;
+  if (slots > 32) slots = 32;
+  return slots < count ? slots : count;
+}
+
 extern "C" int bse_solve_batched(bse_ctx* c, int count, const int* ns, const double* const* A,
                                  const double* const* B, int precision, double* const* lambdas, double* const* Xs,
                                  int* statuses) {
   if (!c || count < 0 || (count > 0 && (!ns || !A || !B || !lambdas))) return BSE_ERR_ARG;
+  if (precision < BSE_FP64 || precision > BSE_MIXED_REFINED) return BSE_ERR_ARG;
+  for (int i = 0; i < count; ++i)
+    if (ns[i] < 1 || ns[i] > 32767 || !A[i] || !B[i]) return BSE_ERR_ARG;
+  if (count == 0) return BSE_OK;
+  BSE_CUDA(cudaSetDevice(c->device));
+  const int slots = batch_slots_for(c, count);
+  // the slot contexts persist in the parent context (their workspaces too)
+  while ((int)c->batch_slots.size() < slots) {
+    bse_ctx* sc = nullptr;
+    BSE_TRY(bse_create(&sc, c->device, c->budget / (size_t)slots));
+    c->batch_slots.push_back(sc);
+  }
+  for (auto* sc : c->batch_slots) sc->budget = c->budget / (size_t)slots;
+  // the caller's stream work comes first
+  BSE_CUDA(cudaStreamSynchronize(c->stream));
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ns[a] > ns[b]; });
+  std::atomic<int> next{0};
+  std::vector<int> rcs(count, BSE_OK);
+  std::vector<std::string> errs(slots);
+  std::vector<std::thread> pool;
+  for (int k = 0; k < slots; ++k) {
+    pool.emplace_back([&, k] {
+      bse_ctx* sc = c->batch_slots[k];
+      cudaSetDevice(sc->device);
+      for (;;) {
+        const int q = next.fetch_add(1);
+        if (q >= count) break;
+        const int i = order[q];
+        const int rc = bse_solve(sc, ns[i], A[i], ns[i], B[i], ns[i], precision, lambdas[i], Xs ? Xs[i] : nullptr,
+                                 nullptr, nullptr, nullptr);
+        rcs[i] = rc;
+        if (rc != BSE_OK && errs[k].empty()) errs[k] = bse_last_error();
+      }
+    });
+  }
+  for (auto& t : pool) t.join();
   int first_err = BSE_OK;
   for (int i = 0; i < count; ++i) {
-    int rc = bse_solve(c, ns[i], A[i], ns[i], B[i], ns[i], precision, lambdas[i], Xs ? Xs[i] : nullptr, nullptr,
-                       nullptr, nullptr);
-    if (statuses) statuses[i] = rc;
-    if (rc != BSE_OK && first_err == BSE_OK) first_err = rc;
+    if (statuses) statuses[i] = rcs[i];
+    if (rcs[i] != BSE_OK && first_err == BSE_OK) first_err = rcs[i];
   }
+  for (auto& e : errs)
+    if (!e.empty()) {
+      record_message(e.c_str());
+      break;
+    }
   return first_err;
 }

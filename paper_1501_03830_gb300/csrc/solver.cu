@@ -69,12 +69,8 @@ size_t workspace_bytes(int n, int precision) {
 }
 
 int Workspace::init(int n_, int precision_) {
-  n = n_;
   precision = precision_;
-  const size_t m = 2 * (size_t)n;
-  const bool f32 = precision != BSE_FP64;
-  const size_t ts = f32 ? 4 : 8;
-  bytes = workspace_bytes(n, precision);
+  bytes = workspace_bytes(n_, precision);
   cudaError_t err = cudaMalloc(&base, bytes);
   if (err != cudaSuccess) {
     cudaGetLastError();
@@ -82,6 +78,15 @@ int Workspace::init(int n_, int precision_) {
     record_error("cudaMalloc(workspace)", err, __FILE__, __LINE__);
     return BSE_ERR_NOMEM;
   }
+  carve(n_);
+  return BSE_OK;
+}
+
+void Workspace::carve(int n_) {
+  n = n_;
+  const size_t m = 2 * (size_t)n;
+  const bool f32 = precision != BSE_FP64;
+  const size_t ts = f32 ? 4 : 8;
   char* p = (char*)base;
   auto take = [&](size_t sz) {
     void* r = p;
@@ -102,7 +107,6 @@ int Workspace::init(int n_, int precision_) {
   Y = (double*)take(16 * m * n);
   status = (DevStatus*)take(64);
   scratch = p;
-  return BSE_OK;
 }
 
 void Workspace::release() {
@@ -150,7 +154,9 @@ extern "C" int bse_destroy(bse_ctx* c) {
   bse_serve_stop(c, 60.0);
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
-  for (auto& kv : c->ws) kv.second.release();
+  for (auto* sc : c->batch_slots) bse_destroy(sc);
+  c->batch_slots.clear();
+  for (auto& w : c->ws) w.release();
   c->ws.clear();
   for (int i = 0; i < 12; ++i) cudaEventDestroy(c->ev[i]);
   cudaStreamDestroy(c->own_stream);
@@ -174,38 +180,42 @@ namespace bse {
 
 size_t ctx_bytes_held(bse_ctx* c) {
   size_t s = 0;
-  for (auto& kv : c->ws) s += kv.second.bytes;
+  for (auto& w : c->ws) s += w.bytes;
   return s;
 }
 
+// A cached workspace of the same precision whose allocation holds the layout
+// for n (the smallest such) is re-carved for n; otherwise a new one is
+// allocated, evicting least recently used ones beyond the HBM budget.
 int get_workspace(bse_ctx* c, int n, int precision, Workspace** out) {
-  const long key = (long)n * 4 + precision;
-  auto it = c->ws.find(key);
-  if (it != c->ws.end()) {
-    it->second.last_use = ++c->use_clock;
-    *out = &it->second;
+  const size_t need = workspace_bytes(n, precision);
+  Workspace* best = nullptr;
+  for (auto& w : c->ws)
+    if (w.precision == precision && w.bytes >= need && (!best || w.bytes < best->bytes)) best = &w;
+  if (best) {
+    if (best->n != n) best->carve(n);
+    best->last_use = ++c->use_clock;
+    *out = best;
     return BSE_OK;
   }
-  const size_t need = workspace_bytes(n, precision);
   if (need > c->budget) {
     record_message("workspace exceeds the context's HBM budget");
     return BSE_ERR_NOMEM;
   }
-  // evict least recently used workspaces until the new one fits the budget
   while (ctx_bytes_held(c) + need > c->budget && !c->ws.empty()) {
     auto victim = c->ws.begin();
     for (auto i = c->ws.begin(); i != c->ws.end(); ++i)
-      if (i->second.last_use < victim->second.last_use) victim = i;
+      if (i->last_use < victim->last_use) victim = i;
     cudaStreamSynchronize(c->stream);
-    victim->second.release();
+    victim->release();
     c->ws.erase(victim);
   }
   Workspace w;
   int rc = w.init(n, precision);
   if (rc != BSE_OK) return rc;
   w.last_use = ++c->use_clock;
-  c->ws[key] = w;
-  *out = &c->ws[key];
+  c->ws.push_back(w);
+  *out = &c->ws.back();
   return BSE_OK;
 }
 

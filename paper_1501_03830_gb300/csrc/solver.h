@@ -1,8 +1,10 @@
 // Host-side state behind the opaque bse_ctx / bse_sol handles.
 #pragma once
 
+#include <list>
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -25,7 +27,8 @@ struct Workspace {
   double *X = nullptr, *Y = nullptr;  // complex128 2n x n
   DevStatus* status = nullptr;
   void* scratch = nullptr;            // stage scratch (max over stages)
-  int init(int n, int precision);
+  int init(int n, int precision);  // allocate workspace_bytes(n, precision) and carve it for n
+  void carve(int n);               // lay the buffers out for n (workspace_bytes(n) <= bytes)
   void release();
 };
 
@@ -43,7 +46,8 @@ struct bse_ctx {
   cudaStream_t stream = nullptr;
   bool timing = false;
   cudaEvent_t ev[12];
-  std::map<long, bse::Workspace> ws;
+  std::list<bse::Workspace> ws;  // a workspace serves every n whose layout fits its bytes
+  std::vector<bse_ctx*> batch_slots;  // per-stream contexts of bse_solve_batched
   unsigned long use_clock = 0;
   bse::ServeState* serve = nullptr;
 };

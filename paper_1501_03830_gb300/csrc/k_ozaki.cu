@@ -58,34 +58,74 @@ size_t ozaki_worksize(int M, int N, int K, int s) {
          al256o(8 * (size_t)N);
 }
 
+// Digits on the integer pipe (FP64 arithmetic is slow on this GPU): x / 2^e is
+// first written as a 62-bit fixed-point integer X (|X| < 2^62; bits below
+// 2^-62 of the vector scale are dropped, far below the s*beta <= 56 bits
+// kept), then digit p is X rounded at bit 62 - beta (p+1) and subtracted:
+// X = sum_p d_p 2^(62 - beta (p+1)) + remainder, |d_0| <= 2^beta,
+// |d_p| <= 2^(beta-1) for p > 0, exactly the balanced digits of the scheme.
+__device__ __forceinline__ long long fixed62(double x, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0) return 0;  // zero or subnormal: below every digit
+  const long long mant = (long long)((b & 0xfffffffffffffULL) | 0x10000000000000ULL);
+  // x = mant 2^(ex - 1075), so X = x 2^(62 - e) = mant 2^(ex - 1013 - e), shift <= 9
+  const int sh = ex - 1013 - e;
+  long long X = sh >= 0 ? (mant << sh) : (sh > -63 ? (mant >> -sh) : 0);
+  return (b >> 63) ? -X : X;
+}
+__device__ __forceinline__ long long fixed62(float x, int e) { return fixed62((double)x, e); }
+
+__device__ __forceinline__ void put_digits(long long X, int beta, int s, long digit_stride,
+                                           __nv_bfloat16* __restrict__ d) {
+  for (int p = 0; p < s; ++p) {
+    const int sh = 62 - beta * (p + 1);
+    long long q = 0;  // digits past the 62 fixed-point bits are zero
+    if (sh > 0) {
+      q = (X + (1LL << (sh - 1))) >> sh;  // round to nearest (ties up)
+      X -= q << sh;
+    }
+    d[p * digit_stride] = __int2bfloat16_rn((int)q);
+  }
+}
+
+// exponent e with max |x| < 2^e (frexp convention), from the largest magnitude's bits
+__device__ __forceinline__ int scale_exp(unsigned long long maxbits) {
+  if (maxbits == 0) return 0;
+  int e = 0;
+  frexp(__longlong_as_double((long long)maxbits), &e);
+  return e;
+}
+
 // One block per K-vector (row of A or column of B): power-of-two scale and digits.
 // Vector v is X[v * ldx + k] (k contiguous).
 template <typename TI>
 __global__ void __launch_bounds__(256) ozaki_split(const TI* __restrict__ X, long ldx, int K, int ldk, int beta,
                                                    int s, long digit_stride, __nv_bfloat16* __restrict__ D,
                                                    double* __restrict__ scale) {
-  __shared__ double red[8];
+  __shared__ unsigned long long red[8];
   const long v = blockIdx.x;
   const TI* x = X + v * ldx;
-  double mx = 0.0;
-  for (int k = threadIdx.x; k < K; k += 256) mx = fmax(mx, fabs((double)x[k]));
-  for (int o = 16; o >= 1; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  // max |x| on the bit patterns (non-negative doubles order like their bits)
+  unsigned long long mx = 0;
+  for (int k = threadIdx.x; k < K; k += 256) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong((double)x[k]) & 0x7fffffffffffffffULL;
+    mx = b > mx ? b : mx;
+  }
+  for (int o = 16; o >= 1; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
-  mx = 0.0;
-  for (int w = 0; w < 8; ++w) mx = fmax(mx, red[w]);
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): |x| / 2^e < 1
+  mx = 0;
+  for (int w = 0; w < 8; ++w) mx = red[w] > mx ? red[w] : mx;
+  const int e = scale_exp(mx);
   if (threadIdx.x == 0) scale[v] = ldexp(1.0, e);
   __nv_bfloat16* dv = D + v * (long)ldk;
   for (int k = threadIdx.x; k < ldk; k += 256) {
-    double r = (k < K && mx > 0.0) ? ldexp((double)x[k], -e) : 0.0;
-    for (int p = 0; p < s; ++p) {
-      const double t = ldexp(r, beta);
-      const double d = rint(t);
-      r = t - d;  // exact
-      dv[p * digit_stride + k] = __float2bfloat16_rn((float)d);
-    }
+    const long long F = (k < K && mx) ? fixed62(x[k], e) : 0;
+    put_digits(F, beta, s, digit_stride, dv + k);
   }
 }
 
@@ -97,23 +137,26 @@ __global__ void __launch_bounds__(256) ozaki_split_rows(const TI* __restrict__ X
                                                         int beta, int s, long digit_stride,
                                                         __nv_bfloat16* __restrict__ D, double* __restrict__ scale) {
   __shared__ double tile[64][33];
-  __shared__ double vmax[8][32];
+  __shared__ unsigned long long vmax[8][32];
   __shared__ int vexp[32];
   const int v0 = blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 x 32
-  // pass 1: per-vector max
-  double mx = 0.0;
+  // pass 1: per-vector max on the bit patterns
+  unsigned long long mx = 0;
   if (v0 + tx < V)
-    for (int k = ty; k < K; k += 8) mx = fmax(mx, fabs((double)X[(v0 + tx) + (long)k * ldx]));
+    for (int k = ty; k < K; k += 8) {
+      const unsigned long long b =
+          (unsigned long long)__double_as_longlong((double)X[(v0 + tx) + (long)k * ldx]) & 0x7fffffffffffffffULL;
+      mx = b > mx ? b : mx;
+    }
   vmax[ty][tx] = mx;
   __syncthreads();
   if (ty == 0) {
-    double m2 = 0.0;
-    for (int w = 0; w < 8; ++w) m2 = fmax(m2, vmax[w][tx]);
-    int e = 0;
-    if (m2 > 0.0) frexp(m2, &e);
-    vexp[tx] = (m2 > 0.0) ? e : 1000000;  // 1e6 marks an all-zero vector
-    if (v0 + tx < V) scale[v0 + tx] = ldexp(1.0, m2 > 0.0 ? e : 0);
+    unsigned long long m2 = 0;
+    for (int w = 0; w < 8; ++w) m2 = vmax[w][tx] > m2 ? vmax[w][tx] : m2;
+    const int e = scale_exp(m2);
+    vexp[tx] = m2 ? e : 1000000;  // 1e6 marks an all-zero vector
+    if (v0 + tx < V) scale[v0 + tx] = ldexp(1.0, m2 ? e : 0);
   }
   __syncthreads();
   // pass 2: digits, 64 k at a time
@@ -131,13 +174,8 @@ __global__ void __launch_bounds__(256) ozaki_split_rows(const TI* __restrict__ X
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int kk = 2 * tx + h;
-        double r = (e == 1000000) ? 0.0 : ldexp(tile[kk][vv], -e);
-        for (int p = 0; p < s; ++p) {
-          const double t = ldexp(r, beta);
-          const double d = rint(t);
-          r = t - d;
-          dv[p * digit_stride + kk] = __float2bfloat16_rn((float)d);
-        }
+        const long long F = (e == 1000000) ? 0 : fixed62(tile[kk][vv], e);
+        put_digits(F, beta, s, digit_stride, dv + kk);
       }
     }
     __syncthreads();

@@ -31,6 +31,7 @@
 
 #include "common.cuh"
 #include "gemm_simt.cuh"
+#include "tc32.cuh"
 #include "internal.cuh"
 #include "../../include/bse_stages.h"
 
@@ -611,7 +612,7 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     // the host vectors must outlive the asynchronous uploads above
     BSE_CUDA(cudaStreamSynchronize(s));
     if (verbose) fprintf(stderr, "[bse refine] n=%d sweep %d: %zu clusters (tau %.1e)\n", n, it, clusters.size(), tau);
-    if (refine_uses_tc(n)) {
+    if (refine_uses_tc(n) && !(tc32::mode() == 1 && n % 2 == 0)) {
       // tensor cores: C1 = U^H R and C2 = U^T R from the one real 2n x 2n product
       // G = [Ur Ui]^T [Rr Ri]; each operand column (an eigenvector, a residual) has a
       // uniform scale, so ~25-bit digits carry these residual-sized products fully
@@ -623,7 +624,8 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
       BSE_LAUNCH_CHECK();
     } else {
       // C1 = U^H R, C2 = U^T R from four real FP32 products (R is residual-sized, so FP32
-      // rounding of these products is eps32 relative to a quantity that is itself small)
+      // rounding of these products is eps32 relative to a quantity that is itself small);
+      // with aligned operands they run on the 3xTF32 tensor-core kernel
       BSE_TRY(gemm<float>(n, n, m, 1.0, w.Urf, m, true, w.Rrf, m, false, 0.0, w.G1, n, s));
       BSE_TRY(gemm<float>(n, n, m, 1.0, w.Uif, m, true, w.Rif, m, false, 0.0, w.G2, n, s));
       BSE_TRY(gemm<float>(n, n, m, 1.0, w.Urf, m, true, w.Rif, m, false, 0.0, w.G3, n, s));

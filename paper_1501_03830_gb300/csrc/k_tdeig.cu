@@ -66,18 +66,22 @@ __global__ void __launch_bounds__(1024) tdeig_prep(int m, const double* __restri
 // ready one step early, so each step has a single FP64 FMA on its dependent
 // path (FP64 latency is long on this GPU; an FP64 division, as in the ratio form
 // p_k / p_{k-1}, is ~20x longer still); the sign tests run on the integer pipe
-// from the bit patterns. A minor that vanishes exactly is replaced by
-// -2^-600 p_{k-1} (the ratio form's guard for a zero pivot: the ratio is taken
-// as tiny and negative). Every 8 steps the pair
+// from the bit patterns. A minor that vanishes exactly is replaced by 2^-900
+// with the sign opposite to p_{k-1} (the ratio form's guard for a zero pivot:
+// the ratio is taken as tiny and negative). Every 8 steps the pair
 // (p_{k-1}, p_k) is rescaled by an exact power of two when it drifts out of
 // [2^-480, 2^480], which changes no sign.
 __device__ __forceinline__ void sturm_step(double ns, double e2k, double& p0, double& p1, int& c) {
   const double t = -e2k * p0;  // off the dependent path
-  double p2 = fma(ns, p1, t);
-  if ((__double_as_longlong(p2) << 1) == 0) p2 = -0x1p-600 * p1;  // exact zero minor (rare)
-  c += (__double_as_longlong(p2) ^ __double_as_longlong(p1)) < 0;
+  const double p2 = fma(ns, p1, t);
+  long long b2 = __double_as_longlong(p2);
+  const long long b1 = __double_as_longlong(p1);
+  // an exactly zero minor becomes 2^-900 with the sign opposite to p_{k-1}
+  // (integer select, no FP64 operation on the dependent path)
+  b2 = ((b2 << 1) == 0) ? ((~b1 & (long long)0x8000000000000000ULL) | 0x07b0000000000000LL) : b2;
+  c += (b2 ^ b1) < 0;
   p0 = p1;
-  p1 = p2;
+  p1 = __longlong_as_double(b2);
 }
 
 __device__ __forceinline__ void sturm_rescale(double& p0, double& p1) {
@@ -101,8 +105,11 @@ __device__ __forceinline__ int sturm_count(int m, const double* __restrict__ e2,
   int c = p1 < 0.0;
   int k = 1;
   for (; k + 8 <= m; k += 8) {
+    double ev[8];  // the block's couplings, loaded before the dependent chain starts
 #pragma unroll
-    for (int u = 0; u < 8; ++u) sturm_step(ns, e2[k - 1 + u], p0, p1, c);
+    for (int u = 0; u < 8; ++u) ev[u] = __ldg(e2 + k - 1 + u);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) sturm_step(ns, ev[u], p0, p1, c);
     sturm_rescale(p0, p1);
   }
   for (; k < m; ++k) sturm_step(ns, e2[k - 1], p0, p1, c);
@@ -154,6 +161,42 @@ __global__ void __launch_bounds__(256) tdeig_msect(int m, int n, const double* _
   if (j < n && gl == 0) lam[j] = 0.5 * (lo + hi);
 }
 
+// Pivots of T - l I from minors: d_k = p_k / p_{k-1} with p the leading
+// (forward) or trailing (backward) minors of the recurrence
+// p_{k+1} = -l p_k - a_k^2 p_{k-1}. The minors carry the dependent chain (one
+// FMA per step); the divisions that give the pivots depend on nothing later, so
+// they overlap with the following steps instead of chaining (an FP64 division
+// is ~0.5 us of latency here). The pair (p_{k-1}, p_k) is rescaled by exact
+// powers of two every 8 steps, which leaves every ratio unchanged.
+struct MinorPair {
+  double p0, p1;  // p_{k-1}, p_k
+};
+
+__device__ __forceinline__ double guard_pivot(double d, double pivmin) { return fabs(d) < pivmin ? -pivmin : d; }
+
+__device__ __forceinline__ void minor_rescale(MinorPair& q) {
+  const int x0 = (int)((__double_as_longlong(q.p0) >> 52) & 0x7ff);
+  const int x1 = (int)((__double_as_longlong(q.p1) >> 52) & 0x7ff);
+  const int x = max(x0, x1);
+  if (x > 1023 + 480) {
+    q.p0 *= 0x1p-480;
+    q.p1 *= 0x1p-480;
+  } else if (x < 1023 - 480) {
+    q.p0 *= 0x1p480;
+    q.p1 *= 0x1p480;
+  }
+}
+
+// p_next = -l p1 - a2 p0 with an exactly zero minor nudged off zero (sign
+// opposite to p1), as in the Sturm count.
+__device__ __forceinline__ double minor_next(double nl, double a2, const MinorPair& q) {
+  const double p2 = fma(nl, q.p1, -a2 * q.p0);
+  long long b2 = __double_as_longlong(p2);
+  const long long b1 = __double_as_longlong(q.p1);
+  b2 = ((b2 << 1) == 0) ? ((~b1 & (long long)0x8000000000000000ULL) | 0x07b0000000000000LL) : b2;
+  return __longlong_as_double(b2);
+}
+
 __global__ void __launch_bounds__(32) tdeig_vectors(int m, int n, const double* __restrict__ e,
                                                     const double* __restrict__ scal,
                                                     const double* __restrict__ lam, double* __restrict__ Vs) {
@@ -161,65 +204,68 @@ __global__ void __launch_bounds__(32) tdeig_vectors(int m, int n, const double* 
   if (j >= n) return;
   const double pivmin = scal[1];
   const double l = lam[j];
+  const double nl = -l;
   double* z = Vs + j;  // z[k * n]
   const long ld = n;
-  // alpha_k = -e[k]; the recurrences below use alpha_k^2 and alpha_k / d.
-  // forward: T - l I = L D L^T, store D
-  double d = -l;
-  if (fabs(d) < pivmin) d = -pivmin;
-  z[0] = d;
+  // forward: D_k = p_k / p_{k-1} (leading minors, p_{-1} = 1, p_0 = -l), stored in z
+  MinorPair f{1.0, nl};
+  if ((__double_as_longlong(f.p1) << 1) == 0) f.p1 = -0x1p-900;
+  z[0] = guard_pivot(f.p1 / f.p0, pivmin);
   for (int k = 0; k < m - 1; ++k) {
-    const double a = -e[k];
-    double dn = -l - a * a / d;
-    if (fabs(dn) < pivmin) dn = -pivmin;
-    z[(long)(k + 1) * ld] = dn;
-    d = dn;
+    const double a = e[k];
+    const double p2 = minor_next(nl, a * a, f);
+    f.p0 = f.p1;
+    f.p1 = p2;
+    z[(long)(k + 1) * ld] = guard_pivot(f.p1 / f.p0, pivmin);
+    if ((k & 7) == 7) minor_rescale(f);
   }
-  // backward: T - l I = U R U^T; gamma_k = D_k + R_k + l (diagonal of T is 0)
-  double rr = -l;
-  if (fabs(rr) < pivmin) rr = -pivmin;
+  // backward: R_k = q_k / q_{k+1} (trailing minors); gamma_k = D_k + R_k + l
+  MinorPair b{1.0, nl};
+  if ((__double_as_longlong(b.p1) << 1) == 0) b.p1 = -0x1p-900;
   int tw = m - 1;
-  double gmin = fabs(z[(long)(m - 1) * ld] + rr + l);
+  double gmin = fabs(z[(long)(m - 1) * ld] + guard_pivot(b.p1 / b.p0, pivmin) + l);
   for (int k = m - 2; k >= 0; --k) {
-    const double a = -e[k];
-    double rn = -l - a * a / rr;
-    if (fabs(rn) < pivmin) rn = -pivmin;
-    rr = rn;
-    const double gk = fabs(z[(long)k * ld] + rr + l);
+    const double a = e[k];
+    const double q2 = minor_next(nl, a * a, b);
+    b.p0 = b.p1;
+    b.p1 = q2;
+    const double rk = guard_pivot(b.p1 / b.p0, pivmin);
+    const double gk = fabs(z[(long)k * ld] + rk + l);
     if (gk < gmin) {
       gmin = gk;
       tw = k;
     }
+    if (((m - 2 - k) & 7) == 7) minor_rescale(b);
   }
-  // recompute R_k for k > tw into z[k]
-  rr = -l;
-  if (fabs(rr) < pivmin) rr = -pivmin;
+  // R_k for k > tw into z[k] (the same backward minors again)
+  MinorPair r{1.0, nl};
+  if ((__double_as_longlong(r.p1) << 1) == 0) r.p1 = -0x1p-900;
   for (int k = m - 1; k > tw; --k) {
-    z[(long)k * ld] = rr;
-    const double a = -e[k - 1];
-    double rn = -l - a * a / rr;
-    if (fabs(rn) < pivmin) rn = -pivmin;
-    rr = rn;
+    z[(long)k * ld] = guard_pivot(r.p1 / r.p0, pivmin);
+    const double a = e[k - 1];
+    const double q2 = minor_next(nl, a * a, r);
+    r.p0 = r.p1;
+    r.p1 = q2;
+    if (((m - 1 - k) & 7) == 7) minor_rescale(r);
   }
-  // upward from the twist: z_{k+1} = -(alpha_k / R_{k+1}) z_k
+  // upward from the twist: z_{k+1} = -(alpha_k / R_{k+1}) z_k (alpha_k = -e[k]);
+  // the quotient is independent of z, only the product chains
   double zk = 1.0;
   double nrm = 1.0;
   for (int k = tw; k < m - 1; ++k) {
-    const double a = -e[k];
-    const double rk1 = z[(long)(k + 1) * ld];
-    const double zn = -(a / rk1) * zk;
+    const double c = e[k] / z[(long)(k + 1) * ld];
+    const double zn = c * zk;
     z[(long)(k + 1) * ld] = zn;
-    nrm += zn * zn;
+    nrm = fma(zn, zn, nrm);
     zk = zn;
   }
   // downward: z_k = -(alpha_k / D_k) z_{k+1}
   zk = 1.0;
   for (int k = tw - 1; k >= 0; --k) {
-    const double a = -e[k];
-    const double dk = z[(long)k * ld];
-    const double zn = -(a / dk) * zk;
+    const double c = e[k] / z[(long)k * ld];
+    const double zn = c * zk;
     z[(long)k * ld] = zn;
-    nrm += zn * zn;
+    nrm = fma(zn, zn, nrm);
     zk = zn;
   }
   z[(long)tw * ld] = 1.0;

@@ -584,12 +584,196 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
   }
 }
 
+
+// ---- small problems: the whole reduction in one CTA --------------------------
+// For m <= TRD_SMALL_MAX the panel scheme's fixed costs per column (two grid
+// barriers, partial-sum buffers) outweigh the work, so one CTA of 512 threads
+// reduces the matrix alone, with only CTA barriers, and many such problems run
+// side by side on the GPU. Unblocked form of the same recurrence: for column
+// j+1, first its own update with (v_j, p_j), then its reflector, then ONE pass
+// over the trailing lower triangle (rows/cols >= j+2, L2-resident at these
+// sizes) that applies A += v_j p_j^T - p_j v_j^T and accumulates the skew SYMV
+// y = A v_{j+1} for the next p = tau y. Warps take 32x32 tiles; lane = row, the
+// row sums accumulate in a register and the column sums (skew: -A^T v) are
+// reduced across the warp by the reduce-scatter butterfly; both go to the
+// warp's own partial vector in shared memory, and the warps' partials are
+// added in a fixed order, so results are reproducible bit for bit.
+constexpr int TRD_SMALL_MAX = 512;
+
+template <typename T>
+__device__ __forceinline__ double cta_sum(double v, double* red32) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red32[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red32[k];
+  return t;
+}
+
+// One pass over the tiles of rows/cols [s, m): optional update with (va, pa),
+// then this warp's share of y = A vb (skew, lower triangle stored) added into
+// its own partial vector `part` (summed over the warps in a fixed order
+// afterwards, so the result does not depend on scheduling). A tile's 32 loads
+// are all issued before any of its stores.
+template <typename T, bool UPDATE>
+__device__ __forceinline__ void small_pass(int m, int s, T* __restrict__ W, long ldw, const T* __restrict__ va,
+                                           const T* __restrict__ pa, const T* __restrict__ vb, T* __restrict__ part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int N = m - s;
+  const int nb = (N + 31) / 32;
+  const int tiles = nb * (nb + 1) / 2;
+  for (int t = warp; t < tiles; t += nwarp) {
+    int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while (I * (I + 1) / 2 > t) --I;
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    const int K = t - I * (I + 1) / 2;
+    const int i = s + 32 * I + lane;
+    const int k0 = s + 32 * K;
+    const bool row_ok = i < m;
+    T* col = W + i;
+    T w[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) w[c] = (row_ok && k0 + c < i) ? col[(long)(k0 + c) * ldw] : T(0);
+    const T vbi = row_ok ? vb[i] : T(0);
+    if (UPDATE) {
+      const T vai = row_ok ? va[i] : T(0);
+      const T pai = row_ok ? pa[i] : T(0);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int k = k0 + c;
+        if (row_ok && k < i) {
+          w[c] = w[c] + vai * pa[k] - pai * va[k];
+          col[(long)k * ldw] = w[c];
+        }
+      }
+    }
+    T dir = T(0);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      dir += w[c] * vb[min(k0 + c, m - 1)];
+      w[c] = -w[c] * vbi;  // column c's term of -A^T vb from this row
+    }
+    warp_reduce_scatter32<T>(w, lane);
+    if (row_ok) part[i] += dir;
+    if (k0 + lane < m) part[k0 + lane] += w[0];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) trd_small_kernel(int m, T* __restrict__ W, long ldw, double* __restrict__ e,
+                                                        T* __restrict__ tau, DevStatus* st) {
+  extern __shared__ __align__(16) unsigned char trd_small_smem[];
+  T* va = reinterpret_cast<T*>(trd_small_smem);  // v_j (global row index)
+  T* pa = va + m;                                // p_j
+  T* vb = pa + m;                                // v_{j+1}
+  T* parts = vb + m;                             // [warps][m] partial sums of A v_{j+1}
+  __shared__ double red32[32];
+  __shared__ double s_alpha;
+  if (st->code) return;
+  const int tid = threadIdx.x, nt = blockDim.x, nwarp = nt >> 5;
+  T* mypart = parts + (long)(tid >> 5) * m;
+  for (int r = tid; r < nwarp * m; r += nt) parts[r] = T(0);
+  // p = tau * (sum of the warps' partials), in warp order; partials cleared
+  auto gather_p = [&](double tauv) {
+    for (int r = tid; r < m; r += nt) {
+      T y = T(0);
+      for (int w = 0; w < nwarp; ++w) {
+        y += parts[(long)w * m + r];
+        parts[(long)w * m + r] = T(0);
+      }
+      pa[r] = (T)tauv * y;
+    }
+  };
+  // column 0: its reflector, then p_0 = tau_0 A v_0 over rows/cols >= 1
+  {
+    double sq = 0.0;
+    for (int r = 2 + tid; r < m; r += nt) {
+      const double w = (double)W[r];
+      sq += w * w;
+    }
+    const double sigma = cta_sum<T>(sq, red32);
+    const House h = make_house((double)W[1], sigma);
+    for (int r = tid; r < m; r += nt) {
+      T v = T(0);
+      if (r >= 1) v = (r == 1) ? T(1) : W[r] * (T)h.scal;
+      va[r] = v;
+      if (r >= 1) W[r] = v;
+    }
+    if (tid == 0) {
+      e[0] = h.beta;
+      tau[0] = (T)h.tau;
+    }
+    __syncthreads();
+    small_pass<T, false>(m, 1, W, ldw, va, va, va, mypart);
+    __syncthreads();
+    gather_p(h.tau);
+    __syncthreads();
+  }
+  for (int j = 0; j + 2 < m; ++j) {
+    // (i) column j+1 gets its update from (v_j, p_j); v_j[j+1] = 1
+    T* cj = W + (long)(j + 1) * ldw;
+    const T pj1 = pa[j + 1];
+    double sq = 0.0;
+    for (int r = j + 2 + tid; r < m; r += nt) {
+      const T w = cj[r] + va[r] * pj1 - pa[r];
+      cj[r] = w;
+      if (r == j + 2) s_alpha = (double)w;
+      else sq += (double)w * (double)w;
+    }
+    const double sigma = cta_sum<T>(sq, red32);  // its barriers also publish s_alpha
+    // (ii) reflector of column j+1
+    const House h = make_house(s_alpha, sigma);
+    for (int r = tid; r < m; r += nt) {
+      T v = T(0);
+      if (r >= j + 2) {
+        v = (r == j + 2) ? T(1) : cj[r] * (T)h.scal;
+        cj[r] = v;
+      }
+      vb[r] = v;
+    }
+    if (tid == 0) {
+      e[j + 1] = h.beta;
+      tau[j + 1] = (T)h.tau;
+    }
+    __syncthreads();
+    // (iii) update + SYMV over rows/cols >= j+2
+    small_pass<T, true>(m, j + 2, W, ldw, va, pa, vb, mypart);
+    __syncthreads();
+    // (iv) p_{j+1} = tau y; v_{j+1} becomes the current reflector
+    gather_p(h.tau);
+    for (int r = tid; r < m; r += nt) va[r] = vb[r];
+    __syncthreads();
+  }
+}
+
 static unsigned long long* g_trace = nullptr;
 static int g_trace_cols = 0;
 
 template <typename T>
 int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStream_t st, DevStatus* status) {
   StatusScope ss(status);
+  if (m <= TRD_SMALL_MAX) {
+    double bytes = 0.0, flops = 0.0;
+    for (int c = 0; c + 1 < m; ++c) {
+      const double N = (double)(m - c - 1);
+      bytes += N * (N - 1.0) * 0.5 * sizeof(T);
+      flops += 2.0 * N * (N - 1.0);
+    }
+    const size_t smem = (3 + 16) * sizeof(T) * (size_t)m;  // v_j, p_j, v_{j+1}, 16 warp partials
+    static cudaError_t attr_err = cudaFuncSetAttribute(trd_small_kernel<T>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)((3 + 16) * sizeof(T) * TRD_SMALL_MAX));
+    if (attr_err != cudaSuccess) {
+      record_error("cudaFuncSetAttribute(trd_small_kernel)", attr_err, __FILE__, __LINE__);
+      return BSE_ERR_CUDA;
+    }
+    KprofScope ks(K_TRD_SYMV, st, bytes, flops);
+    trd_small_kernel<T><<<1, 512, smem, st>>>(m, W, ldw, e, tau, status);
+    BSE_LAUNCH_CHECK();
+    return BSE_OK;
+  }
   TrdWork<T> w = carve<T>(work, m);
   BSE_CUDA(cudaMemsetAsync(w.bar, 0, 64, st));
   int dev = 0, nsm = 0, per_sm = 0;

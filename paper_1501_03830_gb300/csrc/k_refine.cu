@@ -206,6 +206,18 @@ __global__ void __launch_bounds__(256) ref_colstats(int n, const double* __restr
   }
 }
 
+// u_j /= sqrt(b_j), b_j = u_j^H K u_j: exact Theorem 3 normalisation y_j^H x_j = 1.
+__global__ void ref_normalize(int n, double* __restrict__ Ur, double* __restrict__ Ui,
+                              const double* __restrict__ bnorm) {
+  const int j = blockIdx.y;
+  const long m = 2L * n, c = (long)j * m;
+  const double s = rsqrt(bnorm[j]);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long)gridDim.x * blockDim.x) {
+    Ur[i + c] *= s;
+    Ui[i + c] *= s;
+  }
+}
+
 // E from C1 = U^H R, C2 = U^T R (given as G1 = Ur^T Rr, G2 = Ui^T Ri, G3 = Ur^T Ri, G4 = Ui^T Rr).
 __global__ void ref_buildE(int n, const float* __restrict__ G1, const float* __restrict__ G2,
                            const float* __restrict__ G3, const float* __restrict__ G4,
@@ -590,7 +602,35 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     // the Rayleigh quotient's error is second order in the vectors' error, so once
     // a sweep moves the eigenvalues by <= 1e-12 (relative) they are settled
     const bool converged = (res <= res_target && (it > 0 && dl <= 1e-12));
-    if (converged || it >= max_sweeps) break;
+    if (converged || it >= max_sweeps) {
+      // Final polish, no new M U: pairs closer than the first sweep's cluster level
+      // are re-solved by Rayleigh-Ritz on the current (U, P) -- the Newton sweeps
+      // leave their mutual coupling at ~residual / gap, invisible in the residual --
+      // and every column is rescaled to y^H x = 1 exactly.
+      BSE_CUDA(cudaMemcpyAsync(hlam.data(), lam, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
+      BSE_CUDA(cudaStreamSynchronize(s));
+      find_clusters(hlam, fmin(1e-3, fmax(1e-13, 20.0 * dl_level)), clusters, cid);
+      if (!clusters.empty()) {
+        BSE_CUDA(cudaMemcpyAsync(w.clus, clusters.data(), sizeof(int2) * clusters.size(), cudaMemcpyHostToDevice, s));
+        kcount(1);
+        ref_cluster_rr<<<(unsigned)clusters.size(), 256, 0, s>>>(n, w.clus, w.Ur, w.Ui, w.Pr, w.Pi, lam);
+        BSE_LAUNCH_CHECK();
+      }
+      BSE_CUDA(cudaMemsetAsync(w.maxes, 0, 16, s));
+      kcount(2);
+      ref_colstats<<<n, 256, 0, s>>>(n, w.Ur, w.Ui, w.Pr, w.Pi, w.Urf, w.Uif, w.Rrf, w.Rif, lam, w.lam_new, w.bnorm,
+                                     w.scal, w.maxes);
+      BSE_LAUNCH_CHECK();
+      ref_normalize<<<dim3(ceil_div(m, 256 * 4), n), 256, 0, s>>>(n, w.Ur, w.Ui, w.bnorm);
+      BSE_LAUNCH_CHECK();
+      BSE_CUDA(cudaMemcpyAsync(lam, w.lam_new, 8 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+      BSE_CUDA(cudaMemcpyAsync(hm, w.maxes, 16, cudaMemcpyDeviceToHost, s));
+      BSE_CUDA(cudaStreamSynchronize(s));
+      memcpy(&res, &hm[0], 8);
+      if (verbose) fprintf(stderr, "[bse refine] n=%d final: %zu clusters, max scaled residual %.3e\n", n,
+                           clusters.size(), res);
+      break;
+    }
     // clusters: runs closer than ~20x the current eigenvalue error level
     BSE_CUDA(cudaMemcpyAsync(hlam.data(), lam, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
     BSE_CUDA(cudaStreamSynchronize(s));

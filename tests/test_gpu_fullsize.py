@@ -1,0 +1,136 @@
+"""Parity at the full benchmark sizes (n = 2048 and n = 8192), on sampled outputs.
+
+The oracle cannot diagonalize these sizes in a test's time, so it checks what it
+can compute one by one:
+  * eigenvalue positions by Sylvester inertia (oracle.definition.eig_count_below):
+    exactly k eigenvalues lie below lambda_k (1 - 1e-10) and k + 1 below
+    lambda_k (1 + 1e-10), which pins lambda_k to 1e-10 relative (n = 2048);
+  * scaled residuals ||H x_j - lambda_j x_j|| / (||H||_F ||x_j||) of sampled
+    columns against the bar 100 n eps, and biorthogonality y_i^H x_j = delta_ij
+    of sampled pairs (Theorem 3), at both sizes;
+  * the real case (Eq. H-real) at n = 2048: every lambda^2 against the
+    eigenvalues of (A - B)(A + B), computed through the Cholesky factor of A + B
+    as a symmetric eigenproblem.
+The solves run as the benchmark runs them: device-resident inputs and outputs on
+a torch stream.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import definition as D
+from paper_1501_03830_gb300.synth import make_problem
+from tests.helpers import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+EPS = 2.0 ** -52
+
+
+def _solve_dev(torch, p, precision):
+    from paper_1501_03830_gb300 import bse
+
+    n, m = p.n, 2 * p.n
+    A = torch.from_numpy(np.ascontiguousarray(np.asfortranarray(p.A.astype(np.complex128)).T)).cuda()
+    B = torch.from_numpy(np.ascontiguousarray(np.asfortranarray(p.B.astype(np.complex128)).T)).cuda()
+    lam = torch.empty(n, dtype=torch.float64, device="cuda")
+    X = torch.empty(m * n, dtype=torch.complex128, device="cuda")
+    ctx = bse.Context(0)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream.cuda_stream)
+    _, _, _, info, _ = ctx.solve(A, B, precision=precision, out={"lambda": lam, "X": X})
+    torch.cuda.synchronize()
+    ctx.close()
+    return lam, X, info
+
+
+def _columns(torch, X, n, cols):
+    """Columns `cols` of the device 2n x n column-major X, on the host."""
+    Xv = X.view(n, 2 * n)  # row j of the view = column j
+    idx = torch.as_tensor(np.asarray(cols), device=X.device)
+    return np.ascontiguousarray(Xv.index_select(0, idx).cpu().numpy().T)
+
+
+def _biorth(x, n):
+    y = x.copy()
+    y[n:] *= -1.0
+    return np.max(np.abs(y.conj().T @ x - np.eye(x.shape[1])))
+
+
+def _sample(n, k=48):
+    return np.unique(np.concatenate([[0, 1, n // 2, n - 2, n - 1], np.linspace(0, n - 1, k).astype(int)]))
+
+
+def test_fp64_n2048_sampled():
+    torch = torch_cuda()
+    p = make_problem(2048, 2048)
+    n = p.n
+    lam_d, X, info = _solve_dev(torch, p, "fp64")
+    lam = lam_d.cpu().numpy()
+    assert info.status == 0 and np.all(np.diff(lam) >= 0) and lam[0] > 0
+    for k in (0, n // 2, n - 1):
+        assert D.eig_count_below(p.A, p.B, lam[k] * (1 - 1e-10)) == k
+        assert D.eig_count_below(p.A, p.B, lam[k] * (1 + 1e-10)) == k + 1
+    cols = _sample(n)
+    x = _columns(torch, X, n, cols)
+    r = D.scaled_residuals(p.A, p.B, lam[cols], x)
+    assert np.max(r) <= 100 * n * EPS, np.max(r)
+    assert _biorth(x, n) <= 1e-10
+
+
+def test_mixed_refined_n2048_matches_fp64():
+    torch = torch_cuda()
+    p = make_problem(2048, 2048)
+    n = p.n
+    lam64 = _solve_dev(torch, p, "fp64")[0].cpu().numpy()
+    lam_d, X, info = _solve_dev(torch, p, "mixed_refined")
+    lam = lam_d.cpu().numpy()
+    assert info.sweeps >= 1
+    assert np.max(np.abs(lam - lam64) / lam64) <= 1e-10
+    for k in (1, n - 2):
+        assert D.eig_count_below(p.A, p.B, lam[k] * (1 - 1e-10)) == k
+        assert D.eig_count_below(p.A, p.B, lam[k] * (1 + 1e-10)) == k + 1
+    cols = _sample(n)
+    x = _columns(torch, X, n, cols)
+    assert np.max(D.scaled_residuals(p.A, p.B, lam[cols], x)) <= 100 * n * EPS
+    assert _biorth(x, n) <= 1e-10
+
+
+def test_real_case_n2048_all_eigenvalues():
+    """Eq. H-real: lambda^2 = eig((A - B)(A + B)); with A + B = L L^T this is
+    eig(L^T (A - B) L), a symmetric problem."""
+    torch = torch_cuda()
+    p = make_problem(2048, 2049, real=True)
+    n = p.n
+    A = np.tril(p.A) + np.tril(p.A, -1).T
+    B = np.tril(p.B) + np.tril(p.B, -1).T
+    L = np.linalg.cholesky(A + B)
+    ref = np.sqrt(np.sort(sla.eigh(L.T @ (A - B) @ L, eigvals_only=True)))
+    lam = _solve_dev(torch, p, "fp64")[0].cpu().numpy()
+    assert np.max(np.abs(lam - ref) / ref) <= 1e-10
+
+
+def test_mixed_refined_n8192_bench_configuration():
+    """The benchmark's workload (n = 8192, seed 8192, mixed + FP64 refinement):
+    sampled residuals against 100 n eps, sampled biorthogonality, ascending
+    positive spectrum, and agreement of the refined eigenvalues with the
+    residual-based first-order bound |d lambda_j| <= ||r_j|| ||y_j|| / |y_j^H x_j|
+    (y_j^H x_j = 1), evaluated on the sampled columns."""
+    torch = torch_cuda()
+    p = make_problem(8192, 8192)
+    n = p.n
+    lam_d, X, info = _solve_dev(torch, p, "mixed_refined")
+    lam = lam_d.cpu().numpy()
+    assert info.status == 0 and info.sweeps >= 1
+    assert info.refine_resid <= 100 * n * EPS
+    assert np.all(np.diff(lam) >= 0) and lam[0] > 0
+    cols = _sample(n, 24)
+    x = _columns(torch, X, n, cols)
+    r = D.scaled_residuals(p.A, p.B, lam[cols], x)
+    assert np.max(r) <= 100 * n * EPS, np.max(r)
+    assert _biorth(x, n) <= 1e-10
+    # first-order eigenvalue error bound from the sampled residuals
+    normH = np.sqrt(2.0 * (np.linalg.norm(p.A) ** 2 + np.linalg.norm(p.B) ** 2))
+    xn = np.linalg.norm(x, axis=0)
+    bound = r * normH * xn * xn / lam[cols]
+    assert np.max(bound) <= 1e-9, np.max(bound)

@@ -154,6 +154,11 @@ int bse_ozaki_gemm(int M, int N, int K, const double* A, int lda, const double* 
 int bse_tc32_gemm(int M, int N, int K, float alpha, const float* A, int lda, int transA, const float* B, int ldb,
                   int transB, float beta, float* C, int ldc, int uplo, int split, int* dev_status, void* stream);
 
+/* Digit products whose row tiles pair up (an even number of 128-row tiles) run as
+ * 2-CTA clusters sharing each B tile by TMA multicast: 1 (default) on, 0 off (one
+ * CTA per tile). Results are identical either way. Process-wide. */
+int bse_set_tc_pairs(int on);
+
 /* Engine of the FP32 products inside the mixed path: 1 (default) = the 3xTF32
  * tensor-core kernel above wherever the operand layout allows it, 0 = the SIMT
  * FP32 kernel everywhere (for comparisons). Process-wide. */

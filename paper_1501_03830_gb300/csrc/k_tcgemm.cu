@@ -17,6 +17,7 @@
 #include <cuda.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -52,6 +53,31 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
       : "memory");
 }
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
+      "%3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                   smem_u32(bar)),
+               "h"(mask)
+               : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// PAIR = true: the two CTAs of a cluster hold row tiles m0 and m0 + 128 of the
+// same column tile, so they need the same B tile. Each loads one half of it
+// (128 of its 256 rows) and multicasts it into both CTAs' shared memory, and each
+// CTA's MMA-completion commit for a stage is multicast to both CTAs' "empty"
+// barriers (count 2), so neither producer refills a stage the other CTA is still
+// reading. L2 traffic per tile drops from A + B to A + B/2.
+template <bool PAIR>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcParams P) {
@@ -78,10 +104,12 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int n0 = (in_group / gm) * BN;
   const int KB = (P.K + BK - 1) / BK;
 
+  uint32_t crank = 0;
+  if (PAIR) asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], PAIR ? 2 : 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -94,6 +122,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
   tc_fence_before();
   __syncthreads();
+  // the peer may signal this CTA's barriers only after they are initialised
+  if (PAIR) cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
@@ -112,7 +142,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           uint8_t* sa = smem + st * STAGE_BYTES;
           mbar_expect_tx(&full[st], STAGE_BYTES);
           tma_load_2d(sa, &tmA, kb * BK, ya, &full[st]);
-          tma_load_2d(sa + A_BYTES, &tmB, kb * BK, yb, &full[st]);
+          if (PAIR)
+            tma_load_2d_mc(sa + A_BYTES + crank * (B_BYTES / 2), &tmB, kb * BK, yb + (int)crank * (BN / 2), &full[st],
+                           (uint16_t)0x3);
+          else
+            tma_load_2d(sa + A_BYTES, &tmB, kb * BK, yb, &full[st]);
           issued |= 1u << st;
           last_par = (last_par & ~(1u << st)) | (ph << st);
         }
@@ -145,7 +179,10 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk)
             umma_bf16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, (kb | kk) != 0);
-          umma_commit(&empty[st]);
+          if (PAIR)
+            umma_commit_mc(&empty[st], (uint16_t)0x3);
+          else
+            umma_commit(&empty[st]);
         }
         if (ok) umma_commit(&tfull[buf]);
       }
@@ -195,6 +232,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     tmem_dealloc(tmem_base, TMEM_COLS);
   }
   if (threadIdx.x == 0 && *err && P.status) atomicCAS(P.status, 0, *err);
+  // neither CTA leaves while the other may still write its shared memory
+  if (PAIR) cluster_sync_all();
 }
 
 // ---- host side -------------------------------------------------------------
@@ -245,6 +284,9 @@ static int make_map(CUtensorMap* map, const void* base, long rows, long K, long 
   return make_tensor_map_2d(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, K, rows, ldk * 2, BK, box_rows);
 }
 
+static std::atomic<int> g_pair{1};
+static int pair_mode() { return g_pair.load(std::memory_order_relaxed); }
+
 int tc_gemm(const TcProblem& pb, cudaStream_t s) {
   if (pb.M <= 0 || pb.N <= 0 || pb.K <= 0 || pb.units <= 0) return BSE_OK;
   if (pb.units > kMaxUnits || (pb.ldk % 8) != 0 || (reinterpret_cast<uintptr_t>(pb.A) % 16) != 0 ||
@@ -255,15 +297,21 @@ int tc_gemm(const TcProblem& pb, cudaStream_t s) {
   static std::once_flag attr_once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   });
   if (attr_err != cudaSuccess) {
     record_error("cudaFuncSetAttribute(tc_gemm_kernel)", attr_err, __FILE__, __LINE__);
     return BSE_ERR_CUDA;
   }
+  // CTA pairs need an even number of row tiles (the grouped tile order then keeps
+  // every pair on one column tile)
+  const int tiles_m = (pb.M + BM - 1) / BM;
+  const bool pair = pair_mode() && tiles_m % 2 == 0;
   CUtensorMap ma, mb;
   BSE_TRY(make_map(&ma, pb.A, (long)pb.a_rows * pb.a_digits, pb.K, pb.ldk, BM));
-  BSE_TRY(make_map(&mb, pb.B, (long)pb.b_rows * pb.b_digits, pb.K, pb.ldk, BN));
+  BSE_TRY(make_map(&mb, pb.B, (long)pb.b_rows * pb.b_digits, pb.K, pb.ldk, pair ? BN / 2 : BN));
   TcParams P{};
   P.M = pb.M; P.N = pb.N; P.K = pb.K;
   P.a_rows = pb.a_rows; P.b_rows = pb.b_rows;
@@ -277,8 +325,24 @@ int tc_gemm(const TcProblem& pb, cudaStream_t s) {
   P.status = pb.status;
   const long tiles = (long)((pb.M + BM - 1) / BM) * ((pb.N + BN - 1) / BN);
   KprofScope ks(K_GEMM_TC, s, 0.0, 2.0 * pb.M * (double)pb.N * pb.K * pb.units);
-  tc_gemm_kernel<<<(unsigned)tiles, THREADS, SMEM_BYTES, s>>>(ma, mb, P);
-  BSE_LAUNCH_CHECK();
+  if (!pair) {
+    tc_gemm_kernel<false><<<(unsigned)tiles, THREADS, SMEM_BYTES, s>>>(ma, mb, P);
+    BSE_LAUNCH_CHECK();
+    return BSE_OK;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)tiles);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  BSE_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<true>, ma, mb, P));
   return BSE_OK;
 }
 
@@ -296,4 +360,12 @@ extern "C" int bse_tc_gemm_bf16(int M, int N, int K, const void* A, const void* 
   pb.units = 1; pb.a_digit[0] = 0; pb.b_digit[0] = 0; pb.unit_scale[0] = 1.0;
   pb.mode = 0; pb.Cf = C; pb.ldc = ldc; pb.status = dev_status;
   return bse::tc::tc_gemm(pb, (cudaStream_t)stream);
+}
+
+// 1 (default): digit products whose row tiles pair up run as 2-CTA clusters that
+// share their B tiles by TMA multicast; 0: one CTA per tile everywhere.
+extern "C" int bse_set_tc_pairs(int on) {
+  if (on < 0 || on > 1) return BSE_ERR_ARG;
+  bse::tc::g_pair.store(on);
+  return BSE_OK;
 }

@@ -168,3 +168,33 @@ def test_tc32_gemm_rejects_unaligned_pitch():
     rc = L.bse_tc32_gemm(64, 64, 64, 1.0, A.data_ptr(), 65, 0, A.data_ptr(), 65, 0, 0.0, C.data_ptr(), 64, 0, 1,
                          st.data_ptr(), None)
     assert rc == -1
+
+
+@pytest.mark.parametrize("M,N,K,s", [(512, 512, 4096, 8), (1024, 768, 16384, 10)])
+def test_ozaki_cta_pairs_same_result(M, N, K, s):
+    """2-CTA clusters sharing B tiles by multicast give bit-for-bit the result of
+    one CTA per tile, and both are FP64-accurate."""
+    torch = torch_cuda()
+    L, bse = _lib()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(M + K)
+    A = torch.randn(M, K, dtype=torch.float64, device="cuda", generator=g)
+    B = torch.randn(N, K, dtype=torch.float64, device="cuda", generator=g)
+    work = torch.empty(L.bse_ozaki_worksize(M, N, K, s), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")
+    out = []
+    try:
+        for pairs in (0, 1):
+            assert L.bse_set_tc_pairs(pairs) == 0
+            C = torch.zeros(N, M, dtype=torch.float64, device="cuda")
+            bse.check(L.bse_ozaki_gemm(M, N, K, A.data_ptr(), K, B.data_ptr(), K, C.data_ptr(), M, s, work.data_ptr(),
+                                       st.data_ptr(), None), "ozaki")
+            torch.cuda.synchronize()
+            assert int(st[0].item()) == 0
+            out.append(C.t().clone())
+    finally:
+        L.bse_set_tc_pairs(1)
+    assert torch.equal(out[0], out[1])
+    ref = A @ B.t()
+    scale = A.abs().max(dim=1).values[:, None] * B.abs().max(dim=1).values[None, :] * K ** 0.5
+    assert ((out[1] - ref).abs() / scale).max().item() < 1e-13

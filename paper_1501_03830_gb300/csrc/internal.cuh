@@ -41,12 +41,14 @@ struct OzOperand {
   bool strided;
   bool f32;
 };
+// s digits are split for A (and the workspace is laid out for s); s_use <= s of
+// them (and of B's) are paired in this product (0 = all s).
 int ozaki_gemm_ex(const OzOperand& A, const OzOperand& B, int M, int N, int K, double* C, long ldc, int s,
-                  bool accumulate, void* work, bool split_A, int* status, cudaStream_t st);
+                  bool accumulate, void* work, bool split_A, int* status, cudaStream_t st, int s_use = 0);
 int ozaki_gemm(int M, int N, int K, const double* A, long lda, const double* B, long ldb, double* C, long ldc, int s,
-               void* work, bool split_A, int* status, cudaStream_t st);
-// digits per operand for a K-long FP64-accurate product (about 50 bits)
-int ozaki_digits(int K);
+               void* work, bool split_A, int* status, cudaStream_t st, int s_use = 0);
+// digits per operand for a K-long product carrying `bits` bits (50: FP64-accurate)
+int ozaki_digits(int K, int bits = 50);
 
 size_t refine_worksize(int n);
 // FP64 structure-preserving refinement of (lam, X) in place (X: 2n x n complex128, ld 2n),

@@ -47,9 +47,9 @@ static OzakiPlan plan(int M, int N, int K, int s) {
   return p;
 }
 
-int ozaki_digits(int K) {
+int ozaki_digits(int K, int bits) {
   const OzakiPlan p = plan(1, 1, K, 1);
-  return (50 + p.beta - 1) / p.beta;
+  return (bits + p.beta - 1) / p.beta;
 }
 
 size_t ozaki_worksize(int M, int N, int K, int s) {
@@ -189,9 +189,10 @@ __global__ void __launch_bounds__(256) ozaki_split_rows(const TI* __restrict__ X
 // accumulate: add to C instead of overwriting it. split_A = false reuses the A
 // digits already in the workspace (same A, same K, same s).
 int ozaki_gemm_ex(const OzOperand& A, const OzOperand& B, int M, int N, int K, double* C, long ldc, int s,
-                  bool accumulate, void* work, bool split_A, int* status, cudaStream_t st) {
+                  bool accumulate, void* work, bool split_A, int* status, cudaStream_t st, int s_use) {
   if (M <= 0 || N <= 0) return BSE_OK;
   if (s < 1 || s * (s + 1) / 2 > tc::kMaxUnits) return BSE_ERR_ARG;
+  if (s_use <= 0 || s_use > s) s_use = s;
   const OzakiPlan p = plan(M, N, K, s);
   char* w = reinterpret_cast<char*>(work);
   __nv_bfloat16* dA = reinterpret_cast<__nv_bfloat16*>(w);
@@ -201,7 +202,7 @@ int ozaki_gemm_ex(const OzOperand& A, const OzOperand& B, int M, int N, int K, d
   double* rs = reinterpret_cast<double*>(w);
   w += al256o(8 * (size_t)M);
   double* cs = reinterpret_cast<double*>(w);
-  auto split = [&](const OzOperand& X, int V, __nv_bfloat16* D, double* scl) -> int {
+  auto split = [&](const OzOperand& X, int V, __nv_bfloat16* D, double* scl, int s) -> int {
     const double bytes = (X.f32 ? 4.0 : 8.0) * V * (double)K + 2.0 * s * V * (double)p.ldk;
     KprofScope ks(K_ELEMENTWISE, st, bytes, 0.0);
     const long dstride = (long)V * p.ldk;
@@ -222,15 +223,17 @@ int ozaki_gemm_ex(const OzOperand& A, const OzOperand& B, int M, int N, int K, d
     BSE_LAUNCH_CHECK();
     return BSE_OK;
   };
-  if (split_A) BSE_TRY(split(A, M, dA, rs));
-  BSE_TRY(split(B, N, dB, cs));
+  // A keeps all s digits (later calls may reuse them with more digits); B only
+  // needs the s_use digits this product pairs
+  if (split_A) BSE_TRY(split(A, M, dA, rs, s));
+  BSE_TRY(split(B, N, dB, cs, s_use));
   if (!accumulate) BSE_CUDA(cudaMemset2DAsync(C, ldc * sizeof(double), 0, (size_t)M * sizeof(double), N, st));
   tc::TcProblem pb{};
   pb.M = M; pb.N = N; pb.K = K; pb.ldk = p.ldk;
   pb.A = dA; pb.B = dB; pb.a_rows = M; pb.b_rows = N; pb.a_digits = s; pb.b_digits = s;
   int u = 0;
-  for (int a = 0; a < s; ++a)
-    for (int b = 0; a + b < s; ++b) {
+  for (int a = 0; a < s_use; ++a)
+    for (int b = 0; a + b < s_use; ++b) {
       pb.a_digit[u] = a;
       pb.b_digit[u] = b;
       pb.unit_scale[u] = ldexp(1.0, -p.beta * (a + b + 2));
@@ -243,9 +246,9 @@ int ozaki_gemm_ex(const OzOperand& A, const OzOperand& B, int M, int N, int K, d
 
 // C (M x N, column-major, ldc) = A B to FP64 accuracy. work: ozaki_worksize bytes.
 int ozaki_gemm(int M, int N, int K, const double* A, long lda, const double* B, long ldb, double* C, long ldc, int s,
-               void* work, bool split_A, int* status, cudaStream_t st) {
+               void* work, bool split_A, int* status, cudaStream_t st, int s_use) {
   OzOperand a{A, lda, false, false}, b{B, ldb, false, false};
-  return ozaki_gemm_ex(a, b, M, N, K, C, ldc, s, false, work, split_A, status, st);
+  return ozaki_gemm_ex(a, b, M, N, K, C, ldc, s, false, work, split_A, status, st, s_use);
 }
 
 }  // namespace bse

@@ -579,8 +579,12 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     if (refine_uses_tc(n)) {
       // M is symmetric, so its column-major storage is also its K-major row layout;
       // its digits are split once and reused by every sweep
-      BSE_TRY(ozaki_gemm(m, 2 * n, m, M, m, w.Ur, m, w.Pr, m, ozaki_digits(m), w.oz, it == 0,
-                         reinterpret_cast<int*>(st), s));
+      // the first sweep starts from an FP32-level solution (scaled residual ~1e-8):
+      // ~40 bits put the product's error three orders below what that sweep
+      // corrects; every later sweep (and the final check) uses all digits
+      const int sd = ozaki_digits(m);
+      BSE_TRY(ozaki_gemm(m, 2 * n, m, M, m, w.Ur, m, w.Pr, m, sd, w.oz, it == 0, reinterpret_cast<int*>(st), s,
+                         it == 0 ? ozaki_digits(m, 40) : sd));
     } else {
       BSE_TRY(gemm<double>(m, n, m, 1.0, M, m, false, w.Ur, m, false, 0.0, w.Pr, m, s));
       BSE_TRY(gemm<double>(m, n, m, 1.0, M, m, false, w.Ui, m, false, 0.0, w.Pi, m, s));

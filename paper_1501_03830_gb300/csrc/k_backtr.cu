@@ -119,26 +119,28 @@ __global__ void bt_gram_sum(int parts, const double* __restrict__ Gpart, T* __re
 
 // Forward, column-wise triangular factor of a block of reflectors (the
 // compact-WY representation H_0 ... H_{k-1} = I - V T V^T), from G = V^T V.
+// Computed in the path's precision T: on the mixed path its only consumers are
+// FP32 products, and FP32 latency is a small fraction of FP64's on this GPU.
 template <typename T>
 __global__ void bt_larft(int k, const T* __restrict__ G, const T* __restrict__ tau, T* __restrict__ Tf) {
-  __shared__ double Ts[BT_NB][BT_NB + 1];
-  __shared__ double w[BT_NB];
+  __shared__ T Ts[BT_NB][BT_NB + 1];
+  __shared__ T w[BT_NB];
   const int tid = threadIdx.x;
-  for (int e = tid; e < BT_NB * BT_NB; e += blockDim.x) Ts[e % BT_NB][e / BT_NB] = 0.0;
+  for (int e = tid; e < BT_NB * BT_NB; e += blockDim.x) Ts[e % BT_NB][e / BT_NB] = T(0);
   __syncthreads();
   for (int i = 0; i < k; ++i) {
-    const double ti = (double)tau[i];
-    if (tid < i) w[tid] = -ti * (double)G[tid + (long)i * BT_NB];
+    const T ti = tau[i];
+    if (tid < i) w[tid] = -ti * G[tid + (long)i * BT_NB];
     __syncthreads();
     if (tid < i) {
-      double s = 0.0;
+      T s = T(0);
       for (int l = tid; l < i; ++l) s += Ts[tid][l] * w[l];
       Ts[tid][i] = s;
     }
     if (tid == 0) Ts[i][i] = ti;
     __syncthreads();
   }
-  for (int e = tid; e < BT_NB * BT_NB; e += blockDim.x) Tf[e] = (T)Ts[e % BT_NB][e / BT_NB];
+  for (int e = tid; e < BT_NB * BT_NB; e += blockDim.x) Tf[e] = Ts[e % BT_NB][e / BT_NB];
 }
 
 // Phi starts as L: clear the strict upper triangle (it may still hold M).

@@ -487,7 +487,19 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
         T acc = T(0);
         if (q < 2 * c) {
           const int slot = q < c ? q : TRD_NB + (q - c);
-          for (int b = l8d; b < nrb; b += 8) acc += (T)ldcg(a.dotpart + (long)b * 2 * TRD_NB + slot);
+          // independent partial sums so the loads are all in flight at once
+          T pa[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) pa[k] = T(0);
+          int b = l8d;
+          for (; b + 56 < nrb; b += 64) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) pa[k] += (T)ldcg(a.dotpart + (long)(b + 8 * k) * 2 * TRD_NB + slot);
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (b + 8 * k < nrb) pa[k] += (T)ldcg(a.dotpart + (long)(b + 8 * k) * 2 * TRD_NB + slot);
+          acc = ((pa[0] + pa[1]) + (pa[2] + pa[3])) + ((pa[4] + pa[5]) + (pa[6] + pa[7]));
         }
 #pragma unroll
         for (int o = 4; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -508,7 +520,20 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
           const int l = s % TRD_TB;
           T y = T(0);
           for (int q = lane; q < 1; q += 32) y += ldcg(a.Dpart + ((long)0 * maxQ + q) * TRD_TB + l);
-          for (int R2 = lane; R2 < ns; R2 += 32) y += ldcg(a.Tpart + ((long)0 * ns + R2) * TRD_TB + l);
+          {
+            T py[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) py[k] = T(0);
+            int R2 = lane;
+            for (; R2 + 224 < ns; R2 += 256) {
+#pragma unroll
+              for (int k = 0; k < 8; ++k) py[k] += ldcg(a.Tpart + ((long)0 * ns + R2 + 32 * k) * TRD_TB + l);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (R2 + 32 * k < ns) py[k] += ldcg(a.Tpart + ((long)0 * ns + R2 + 32 * k) * TRD_TB + l);
+            y += ((py[0] + py[1]) + (py[2] + py[3])) + ((py[4] + py[5]) + (py[6] + py[7]));
+          }
           for (int t = lane; t < c; t += 32) y += sVs[t] * sdP[t] - sPs[t] * sdV[t];
 #pragma unroll
           for (int o = 16; o >= 1; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);

@@ -15,6 +15,7 @@
 // one elementwise epilogue that writes X and Y as interleaved complex128.
 #include "common.cuh"
 #include "gemm_simt.cuh"
+#include "internal.cuh"
 #include "../../include/bse_stages.h"
 
 namespace bse {
@@ -32,10 +33,16 @@ static inline long bt_ld(long x) { return (x + 31) / 32 * 32; }
 template <typename T>
 struct BtWork {
   T *Vb, *Z, *Z2, *G, *Gpart, *Tf, *Fre, *Fim, *Vsf;
+  void* oz;  // digit-split product workspace (FP64 path)
   long ldv, ldvs;
 };
 
 static inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// The FP64 path's two m x n x n eigenvector products run FP64-accurate on the
+// bf16 tensor cores (digit-split product) from this size on; below it, and for
+// every FP32 product, the GEMM kernels.
+constexpr int BT_OZAKI_MIN_N = 256;
 
 template <typename T>
 size_t bt_worksize(int m) {
@@ -45,6 +52,7 @@ size_t bt_worksize(int m) {
   b += al256(sizeof(double) * parts * BT_NB * BT_NB);
   b += 2 * al256(sizeof(T) * (size_t)m * n);
   if (sizeof(T) == 4) b += al256(sizeof(T) * (size_t)m * bt_ld(n));
+  if (sizeof(T) == 8 && (int)n >= BT_OZAKI_MIN_N) b += al256(ozaki_worksize(m, (int)n, (int)n, ozaki_digits((int)n)));
   return b;
 }
 
@@ -65,6 +73,8 @@ static BtWork<T> carve_bt(void* work, int m) {
   w.Fre = (T*)p; p += al256(sizeof(T) * (size_t)m * n);
   w.Fim = (T*)p; p += al256(sizeof(T) * (size_t)m * n);
   w.Vsf = (sizeof(T) == 4) ? (T*)p : nullptr;
+  if (sizeof(T) == 4) p += al256(sizeof(T) * (size_t)m * bt_ld(n));
+  w.oz = p;
   return w;
 }
 
@@ -240,8 +250,21 @@ int backtransform(int m, T* L, long ldl, const T* W, long ldw, const T* tau, con
     Vsx = reinterpret_cast<const T*>(Vs);
   }
   // F_re = Phi[:, even] Vs[even, :],  F_im = Phi[:, odd] Vs[odd, :]
-  BSE_TRY(gemm<T>(m, n, n, 1.0, L, 2 * ldl, false, Vsx, 2L * ldvs, true, 0.0, w.Fre, m, s));
-  BSE_TRY(gemm<T>(m, n, n, 1.0, L + ldl, 2 * ldl, false, Vsx + ldvs, 2L * ldvs, true, 0.0, w.Fim, m, s));
+  if (sizeof(T) == 8 && n >= BT_OZAKI_MIN_N) {
+    // row i of Phi[:, even] is L[i + 2k ldl] (k = 0..n-1), column j of Vs[even, :]
+    // is Vs[2k n + j]: both strided K-vectors
+    int* zst = reinterpret_cast<int*>(current_status());
+    const int sd = ozaki_digits(n);
+    for (int h = 0; h < 2; ++h) {
+      OzOperand a{L + h * ldl, 2 * ldl, true, false};
+      OzOperand b{Vs + h * (long)n, 2L * n, true, false};
+      BSE_TRY(ozaki_gemm_ex(a, b, m, n, n, reinterpret_cast<double*>(h ? w.Fim : w.Fre), m, sd, false, w.oz, true,
+                            zst, s));
+    }
+  } else {
+    BSE_TRY(gemm<T>(m, n, n, 1.0, L, 2 * ldl, false, Vsx, 2L * ldvs, true, 0.0, w.Fre, m, s));
+    BSE_TRY(gemm<T>(m, n, n, 1.0, L + ldl, 2 * ldl, false, Vsx + ldvs, 2L * ldvs, true, 0.0, w.Fim, m, s));
+  }
   {
     KprofScope ks(K_ELEMENTWISE, s, 2.0 * sizeof(T) * m * (double)n + 32.0 * m * (double)n, 0.0);
     bt_epilogue<T><<<dim3(ceil_div(n, 128), n), 128, 0, s>>>(n, w.Fre, w.Fim, m, lam, reinterpret_cast<double2*>(X),

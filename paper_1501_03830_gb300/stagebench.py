@@ -42,7 +42,8 @@ def run(argv=None) -> dict:
     ap.add_argument("--split", type=int, default=1, help="tc32: 1 = 3xTF32, 0 = one TF32 pass")
     ap.add_argument("--m", type=int, default=8192, help="matrix order (tridiag, tdeig)")
     ap.add_argument("--fp64", action="store_true", help="tridiag in FP64 instead of FP32")
-    ap.add_argument("--pairs", type=int, default=1, help="ozaki: 2-CTA clusters sharing B tiles (1) or not (0)")
+    ap.add_argument("--pairs", type=int, default=1,
+                    help="ozaki: 4x2 multicast clusters (2), 2x1 (1) or one CTA per tile (0)")
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
     L = bse.lib()

@@ -170,10 +170,11 @@ def test_tc32_gemm_rejects_unaligned_pitch():
     assert rc == -1
 
 
-@pytest.mark.parametrize("M,N,K,s", [(512, 512, 4096, 8), (1024, 768, 16384, 10)])
+@pytest.mark.parametrize("M,N,K,s", [(512, 512, 4096, 8), (1024, 768, 16384, 10), (1024, 1024, 8192, 10)])
 def test_ozaki_cta_pairs_same_result(M, N, K, s):
-    """2-CTA clusters sharing B tiles by multicast give bit-for-bit the result of
-    one CTA per tile, and both are FP64-accurate."""
+    """Clusters sharing operand tiles by multicast (4 x 2 where the tile grid allows,
+    else 2 x 1) give bit-for-bit the result of one CTA per tile, and are
+    FP64-accurate."""
     torch = torch_cuda()
     L, bse = _lib()
     g = torch.Generator(device="cuda")
@@ -184,7 +185,7 @@ def test_ozaki_cta_pairs_same_result(M, N, K, s):
     st = torch.zeros(4, dtype=torch.int32, device="cuda")
     out = []
     try:
-        for pairs in (0, 1):
+        for pairs in (0, 1, 2):
             assert L.bse_set_tc_pairs(pairs) == 0
             C = torch.zeros(N, M, dtype=torch.float64, device="cuda")
             bse.check(L.bse_ozaki_gemm(M, N, K, A.data_ptr(), K, B.data_ptr(), K, C.data_ptr(), M, s, work.data_ptr(),
@@ -193,8 +194,8 @@ def test_ozaki_cta_pairs_same_result(M, N, K, s):
             assert int(st[0].item()) == 0
             out.append(C.t().clone())
     finally:
-        L.bse_set_tc_pairs(1)
-    assert torch.equal(out[0], out[1])
+        L.bse_set_tc_pairs(2)
+    assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
     ref = A @ B.t()
     scale = A.abs().max(dim=1).values[:, None] * B.abs().max(dim=1).values[None, :] * K ** 0.5
     assert ((out[1] - ref).abs() / scale).max().item() < 1e-13

@@ -205,6 +205,16 @@ def workload_config(args) -> dict:
 
 # --- our GPU path -----------------------------------------------------------------
 
+def aggregate_ranks(torch, dist, t_ms: float, ws: int, steps: int, device) -> tuple[float, float]:
+    """Whole-job throughput of `ws` replicas that each solved `steps` problems:
+    the slowest rank's time (max over ranks) and all ranks' solves / that time."""
+    t_max = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    t_ms = float(t_max.item())
+    return t_ms, ws * steps / (t_ms * 1e-3)
+
+
 def to_dev_colmajor(torch, a, device):
     import numpy as np
 
@@ -273,11 +283,7 @@ def run_ours(args):
     launches = bse.launch_count() - launches0
     clocks = sampler.stop()
     t_ms = ev0.elapsed_time(ev1)
-    t_max = torch.tensor([t_ms], dtype=torch.float64, device=device)
-    if ws > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    t_ms = float(t_max.item())
-    value = ws * args.steps / (t_ms * 1e-3)
+    t_ms, value = aggregate_ranks(torch, dist, t_ms, ws, args.steps, device)
     last = infos[-1]
 
     # instrumented run: per-kernel-class device time (CUDA events on the launch stream)
@@ -364,33 +370,70 @@ def run_ours(args):
     return 0
 
 
+# kernel class -> the source files its kernels are built from (a recorded ncu
+# traffic figure is only used while these are unchanged)
+KERNEL_SOURCES = {"gemm_tc": ["k_tcgemm.cu", "k_ozaki.cu", "tcgemm.cuh", "ptx_sm100.cuh"],
+                  "trd_symv": ["k_tridiag.cu"], "gemm_tf32": ["k_tc32.cu", "ptx_sm100.cuh"]}
+
+
+def sources_sha256(files) -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1501_03830_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(name: str):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
+    committed ncu summary profiles/traffic_<class>_*.md, if its source hash matches."""
+    import glob
+    import re
+
+    if name not in KERNEL_SOURCES:
+        return None
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"traffic_{name}_*.md"))):
+        with open(path) as f:
+            text = f.read()
+        h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+        b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+        if h and b and h.group(1) == sources_sha256(KERNEL_SOURCES[name]):
+            return float(b.group(1))
+    return None
+
+
 def roofline(kp: dict, peaks: dict, torch, device) -> dict:
     """Roofline entry for the kernel class with the most device time."""
     top = max(kp.items(), key=lambda kv: kv[1]["ms"])
     name, st = top
     if st["ms"] <= 0:
         return None
+    traffic = recorded_traffic(name)
     sec = st["ms"] * 1e-3
     if name in ("trd_symv", "weights", "form_M", "elementwise", "tdeig_vec"):
         achieved = st["bytes"] / sec / 1e9
         peak = float(peaks.get("hbm_gbs"))
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "launches": st["launches"],
+                "frac": achieved / peak, "traffic": traffic, "launches": st["launches"],
                 "avg_launch_ms": st["ms"] / max(1, st["launches"]),
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peaks['_source']})"}
     if name == "gemm_tc":
         achieved = st["flops"] / sec / 1e12
         peak = float(peaks.get("bf16_tflops"))
         return {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "launches": st["launches"],
+                "frac": achieved / peak, "traffic": traffic, "launches": st["launches"],
                 "avg_launch_ms": st["ms"] / max(1, st["launches"]),
-                "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({peaks['_source']})"}
+                "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({peaks['_source']})",
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch on this workload "
+                                  "(profiles/traffic_gemm_tc_n8192_mixed_refined.md)" if traffic else None}
     if name == "gemm_tf32":
         # 3xTF32: three TF32 tensor passes per FP32 product; TF32 peak = measured bf16 x 1.1/2.25 (nominal ratio)
         achieved = st["flops"] / sec / 1e12
         peak = float(peaks.get("bf16_tflops")) * (1.1 / 2.25) / 3.0
         return {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "launches": st["launches"],
+                "frac": achieved / peak, "traffic": traffic, "launches": st["launches"],
                 "avg_launch_ms": st["ms"] / max(1, st["launches"]),
                 "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({peaks['_source']}) x 1.1/2.25 (TF32) / 3 "
                                "(3xTF32 passes per FP32 flop)"}

@@ -579,12 +579,14 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     if (refine_uses_tc(n)) {
       // M is symmetric, so its column-major storage is also its K-major row layout;
       // its digits are split once and reused by every sweep
-      // the first sweep starts from an FP32-level solution (scaled residual ~1e-8):
-      // ~40 bits put the product's error three orders below what that sweep
-      // corrects; every later sweep (and the final check) uses all digits
+      // bits of the product per sweep: the first sweep starts from an FP32-level
+      // solution (scaled residual ~1e-8), where ~40 bits put the product's error
+      // three orders below what that sweep corrects; every later sweep (and the
+      // final check, whose Rayleigh quotients must settle to 1e-12) uses all digits
       const int sd = ozaki_digits(m);
+      const int bits = it == 0 ? 40 : 50;
       BSE_TRY(ozaki_gemm(m, 2 * n, m, M, m, w.Ur, m, w.Pr, m, sd, w.oz, it == 0, reinterpret_cast<int*>(st), s,
-                         it == 0 ? ozaki_digits(m, 40) : sd));
+                         std::min(sd, ozaki_digits(m, bits))));
     } else {
       BSE_TRY(gemm<double>(m, n, m, 1.0, M, m, false, w.Ur, m, false, 0.0, w.Pr, m, s));
       BSE_TRY(gemm<double>(m, n, m, 1.0, M, m, false, w.Ui, m, false, 0.0, w.Pi, m, s));

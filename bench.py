@@ -600,16 +600,21 @@ def run_serving(args):
     # warm every kernel once (a small and a large size)
     for q in (pool[int(np.argmin(pool_n))], pool[int(np.argmax(pool_n))]):
         ctx.solve(q.A, q.B, precision=args.precision)
-    # result buffers per distinct problem: requests of the same problem write the same bits
-    bufs = {}
+    # inputs and result buffers in pinned host memory, one set per distinct problem
+    # (requests of the same problem write the same bits)
+    pinned, bufs = {}, {}
     for p in probs:
         if id(p) not in bufs:
-            bufs[id(p)] = (np.empty(p.n), np.empty((2 * p.n, p.n), dtype=np.complex128, order="F"))
+            pinned[id(p)] = (torch.from_numpy(np.ascontiguousarray(np.asfortranarray(p.A).T)).pin_memory(),
+                             torch.from_numpy(np.ascontiguousarray(np.asfortranarray(p.B).T)).pin_memory())
+            bufs[id(p)] = (torch.empty(p.n, dtype=torch.float64).pin_memory(),
+                           torch.empty(2 * p.n * p.n, dtype=torch.complex128).pin_memory())
     outs = [bufs[id(p)] for p in probs]
 
     def run_stream(arrivals, precision):
         ctx.serve_start(slots)
-        reqs = [bse.make_request(p.n, p.A, p.B, o[0], o[1], precision=precision) for p, o in zip(probs, outs)]
+        reqs = [bse.make_request(p.n, pinned[id(p)][0], pinned[id(p)][1], o[0], o[1], precision=precision)
+                for p, o in zip(probs, outs)]
         tickets = [None] * len(probs)
         done = {}
         t0 = time.perf_counter()
@@ -658,7 +663,7 @@ def run_serving(args):
         p = probs[i]
         if id(p) not in refs:
             refs[id(p)] = D.solve(p.A, p.B).lam
-        worst = max(worst, float(np.max(np.abs(outs[i][0] - refs[id(p)]) / np.abs(refs[id(p)]))))
+        worst = max(worst, float(np.max(np.abs(outs[i][0].numpy() - refs[id(p)]) / np.abs(refs[id(p)]))))
     ns = [p.n for p in probs]
     out = {
         "metric": "serving: BSE solves/s and p50/p99 latency (Poisson stream, mixed+refined)",
@@ -667,7 +672,7 @@ def run_serving(args):
         "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": f"{len(probs)} requests, n log-uniform in [64, 4096] with "
                                f"{sum(1 for k in picks if k < 0)} at n = 8192, Poisson arrivals at 0.8 x measured "
-                               f"capacity ({rate:.3f} req/s), host buffers, {slots} slots",
+                               f"capacity ({rate:.3f} req/s), pinned host buffers, {slots} slots",
                    "pool": f"{len(pool)} distinct seeded problems + 1 at n = 8192",
                    "sum_n3": float(sum(float(n) ** 3 for n in ns))},
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),

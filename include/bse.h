@@ -120,7 +120,9 @@ int bse_spectrum(bse_ctx* ctx, const bse_sol* sol, const double* d_r, const doub
  * complex128, ld 2n). The pointers stay owned by the solution. */
 int bse_sol_view(const bse_sol* sol, int* n, const double** lambda_dev, const double** X_dev);
 
-/* Free a kept solution. Safe on NULL. */
+/* Free a kept solution. Safe on NULL. Its device memory goes back to the
+ * device's memory pool (stream-ordered allocator), where later kept solutions
+ * reuse it without a device-wide synchronisation. */
 int bse_sol_free(bse_sol* sol);
 
 /* ---- request queue with continuous batching ---------------------------- */

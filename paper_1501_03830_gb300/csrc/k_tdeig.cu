@@ -290,7 +290,7 @@ int tdeig(int m, const double* e, double* lam, double* Vs, double* work, DevStat
     // few enough not to waste FP64 throughput on large problems
     KprofScope ks(K_TDEIG_BISECT, s, 0.0, 0.0);
     if (n >= 4096)
-      tdeig_msect<8><<<ceil_div((long)n * 8, 256), 256, 0, s>>>(m, n, e2, scal, lam, st);
+      tdeig_msect<4><<<ceil_div((long)n * 4, 256), 256, 0, s>>>(m, n, e2, scal, lam, st);
     else if (n >= 1024)
       tdeig_msect<16><<<ceil_div((long)n * 16, 256), 256, 0, s>>>(m, n, e2, scal, lam, st);
     else

@@ -145,6 +145,14 @@ extern "C" int bse_create(bse_ctx** out, int device, size_t hbm_budget) {
   }
   c->stream = c->own_stream;
   for (int i = 0; i < 12; ++i) cudaEventCreate(&c->ev[i]);
+  // kept solutions and host-staging buffers come from the device's default
+  // memory pool; let it cache freed blocks instead of returning them at every
+  // synchronisation (a process-local setting of this library's allocations)
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t keep_all = ~0ULL;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep_all);
+  }
   *out = c;
   return BSE_OK;
 }
@@ -377,7 +385,10 @@ extern "C" int bse_solve(bse_ctx* c, int n, const double* A, int lda, const doub
     bse_sol* sol = new bse_sol();
     sol->n = n;
     sol->device = c->device;
-    if (cudaMalloc(&sol->lam, 8 * (size_t)n) != cudaSuccess || cudaMalloc(&sol->X, 16 * (size_t)m * n) != cudaSuccess) {
+    // stream-ordered allocations from the device pool (which keeps freed memory
+    // cached, see bse_create): no device-wide synchronisation per kept solution
+    if (cudaMallocAsync((void**)&sol->lam, 8 * (size_t)n, s) != cudaSuccess ||
+        cudaMallocAsync((void**)&sol->X, 16 * (size_t)m * n, s) != cudaSuccess) {
       cudaGetLastError();
       bse_sol_free(sol);
       record_message("bse_solve: cannot allocate the kept solution");
@@ -401,8 +412,11 @@ extern "C" int bse_sol_view(const bse_sol* sol, int* n, const double** lambda_de
 
 extern "C" int bse_sol_free(bse_sol* sol) {
   if (!sol) return BSE_OK;
-  if (sol->lam) cudaFree(sol->lam);
-  if (sol->X) cudaFree(sol->X);
+  // every call that used the solution has synchronised its stream before
+  // returning, so the blocks can go back to the pool in the default stream's order
+  // (valid even after the context that made the solution is destroyed)
+  if (sol->lam) cudaFreeAsync(sol->lam, 0);
+  if (sol->X) cudaFreeAsync(sol->X, 0);
   delete sol;
   return BSE_OK;
 }

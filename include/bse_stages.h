@@ -126,7 +126,8 @@ int bse_stage_refine(int n, const double* M, double* lam, double* X, int max_swe
 
 /* C (M x N FP32, column-major, ldc) = A B^T on the tcgen05 tensor cores, with
  * A: M x K bf16 and B: N x K bf16, both K-contiguous with row pitch ldk
- * (ldk >= K, ldk % 8 == 0, bases 16-byte aligned). FP32 accumulation. A bounded
+ * (ldk >= K, ldk % 8 == 0, bases 16-byte aligned). FP32 accumulation: the tensor
+ * cores sum 256-deep chunks, the chunks are added in FP32 registers. A bounded
  * internal wait that gives up stores BSE_ERR_TIMEOUT in dev_status. */
 int bse_tc_gemm_bf16(int M, int N, int K, const void* A, const void* B, int ldk, float* C, int ldc, int* dev_status,
                      void* stream);
@@ -135,10 +136,16 @@ int bse_tc_gemm_bf16(int M, int N, int K, const void* A, const void* B, int ldk,
  * tensor cores by error-free digit splitting (Ozaki scheme): row i of A is the
  * K-vector A + i*lda (for a symmetric matrix stored column-major, the matrix
  * itself), column j of B is B + j*ldb. s digits of beta bits per operand
- * (beta = floor((24 - log2 K)/2), at most 7) give about beta*s bits relative to
- * the largest entry of each row of A times that of each column of B;
- * s (s+1)/2 <= 72 tensor-core passes. work: bse_ozaki_worksize bytes. */
+ * (beta = bse_ozaki_digit_bits(K): 7 for 256 <= K <= 32768) give about beta*s
+ * bits relative to the largest entry of each row of A times that of each column
+ * of B; 1 <= s <= 11, s (s+1)/2 tensor-core passes (digit pairs p + q < s). The
+ * tensor cores sum each pair exactly over 256-deep chunks and the chunks are
+ * added as integers, so the result does not depend on the launch shape.
+ * work: bse_ozaki_worksize bytes. */
 size_t bse_ozaki_worksize(int M, int N, int K, int s);
+/* Digit width beta (bits) the digit-split product uses for reduction length K
+ * (K >= 1; BSE_ERR_ARG otherwise). */
+int bse_ozaki_digit_bits(int K);
 int bse_ozaki_gemm(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C, int ldc, int s,
                    void* work, int* dev_status, void* stream);
 

@@ -44,6 +44,7 @@ EXPORTS = [
     "bse_stage_tridiag_worksize", "bse_stage_tridiag", "bse_debug_trace_tridiag", "bse_stage_tridiag_grid", "bse_stage_tdeig_worksize", "bse_stage_tdeig", "bse_stage_tdeig_noalloc",
     "bse_stage_backtransform_worksize", "bse_stage_backtransform", "bse_stage_weights",
     "bse_stage_refine_worksize", "bse_stage_refine", "bse_tc_gemm_bf16", "bse_ozaki_worksize", "bse_ozaki_gemm",
+    "bse_ozaki_digit_bits",
     "bse_tc32_gemm", "bse_set_fp32_gemm", "bse_set_tc_pairs",
 ]
 
@@ -125,6 +126,7 @@ def lib() -> C.CDLL:
         "bse_stage_refine": (i, [i, vp, vp, vp, i, vp, vp, vp, C.POINTER(i), C.POINTER(d)]),
         "bse_tc_gemm_bf16": (i, [i, i, i, vp, vp, i, vp, i, vp, vp]),
         "bse_ozaki_worksize": (sz, [i, i, i, i]),
+        "bse_ozaki_digit_bits": (i, [i]),
         "bse_ozaki_gemm": (i, [i, i, i, vp, i, vp, i, vp, i, i, vp, vp, vp]),
         "bse_tc32_gemm": (i, [i, i, i, C.c_float, vp, i, i, vp, i, i, C.c_float, vp, i, i, i, vp, vp]),
         "bse_set_fp32_gemm": (i, [i]),

@@ -6,12 +6,16 @@
 //
 // sigma_i, tau_j are powers of two bounding row i of A and column j of B, and
 // the digits a^(p), b^(q) are integers with |digit| <= 2^beta, exactly
-// representable in bf16. beta is chosen so that K * 2^(2 beta) <= 2^24: every
-// dot product of two digit vectors is then an integer below 2^24, which the
-// tensor cores' FP32 accumulation holds exactly whatever the summation order.
-// Each digit pair (p, q) with p + q < s is one tensor-core pass; the epilogue
-// accumulates sigma_i tau_j 2^{-beta (p+q+2)} x (exact integer) in FP64. With s
-// digits per operand the result carries about beta*s bits relative to
+// representable in bf16. The tensor cores accumulate a digit pair's products
+// in FP32 over chunks of Kc = 256 (kTcChunkK) reduction steps; beta is chosen so
+// that Kc * 2^(2 beta) <= 2^22: every chunk sum is then an integer the FP32
+// accumulation holds exactly whatever its summation order, and the epilogue
+// adds the chunk sums in 32-bit integers (which bounds the whole-K sum of one
+// anti-diagonal of pairs below 2^31, a second condition on beta). Each digit
+// pair (p, q) with p + q < s is one tensor-core pass; the pairs of one
+// anti-diagonal p + q = d share their scale and their integer sum, and the
+// epilogue adds sigma_i tau_j 2^{-beta (d+2)} x (exact integer) to C in FP64.
+// With s digits per operand the result carries about beta*s bits relative to
 // sigma_i tau_j.
 //
 // Layout: A is given K-major (row i of A is A[i * lda + k], k contiguous; for a
@@ -33,16 +37,28 @@ struct OzakiPlan {
   int M, N, K, ldk, beta, s;
 };
 
+constexpr int kTcChunkK = 256;  // reduction steps per exact FP32 chunk (4 blocks of 64)
+constexpr int kMaxDigits = 11;  // s (s + 1) / 2 <= kMaxUnits
+
+static int ceil_log2(long x) {
+  int l = 0;
+  while ((1L << l) < x) ++l;
+  return l;
+}
+
 static OzakiPlan plan(int M, int N, int K, int s) {
   OzakiPlan p;
   p.M = M; p.N = N; p.K = K;
   p.ldk = (K + 63) / 64 * 64;
-  // K * 2^(2 beta) <= 2^24
-  int lk = 0;
-  while ((1L << lk) < (long)p.ldk) ++lk;
-  p.beta = (24 - lk) / 2;
-  if (p.beta > 7) p.beta = 7;
-  if (p.beta < 1) p.beta = 1;
+  // chunk sums exact in FP32 and convertible by the 1.5 * 2^23 shift:
+  // Kc * 2^(2 beta) <= 2^22; bf16 holds |digit| <= 2^8 exactly
+  const int lkc = ceil_log2(p.ldk < kTcChunkK ? p.ldk : kTcChunkK);
+  p.beta = (22 - lkc) / 2;
+  if (p.beta > 8) p.beta = 8;
+  // one anti-diagonal's integer sum over the whole K stays below 2^31:
+  // |sum| <= K 2^(2 beta) (1 + (d - 1) / 4) with d <= kMaxDigits - 1
+  while (p.beta > 1 && (double)p.ldk * ldexp(1.0, 2 * p.beta) * (1.0 + (kMaxDigits - 2) / 4.0) >= 2147483648.0)
+    --p.beta;
   p.s = s;
   return p;
 }
@@ -52,10 +68,11 @@ int ozaki_digits(int K, int bits) {
   return (bits + p.beta - 1) / p.beta;
 }
 
+// digits of A and B, their scales, and one int32 M x N plane per anti-diagonal
 size_t ozaki_worksize(int M, int N, int K, int s) {
   OzakiPlan p = plan(M, N, K, s);
   return al256o((size_t)2 * s * M * p.ldk) + al256o((size_t)2 * s * N * p.ldk) + al256o(8 * (size_t)M) +
-         al256o(8 * (size_t)N);
+         al256o(8 * (size_t)N) + al256o((size_t)4 * s * M * N);
 }
 
 // Digits on the integer pipe (FP64 arithmetic is slow on this GPU): x / 2^e is
@@ -182,6 +199,27 @@ __global__ void __launch_bounds__(256) ozaki_split_rows(const TI* __restrict__ X
   }
 }
 
+// C (+)= sigma_i tau_j sum_d 2^{-beta (d+2)} S_d(i, j): the G anti-diagonal
+// integer sums S_d (int32 planes, M x N column-major, ld M) scaled and added in
+// FP64, smallest terms first (Horner in 2^-beta, exact power-of-two steps).
+__global__ void __launch_bounds__(256) ozaki_combine(int M, int N, int G, const int* __restrict__ S, long plane,
+                                                     const double* __restrict__ rs, const double* __restrict__ cs,
+                                                     int beta, double* __restrict__ C, long ldc, int accumulate) {
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  if (i >= M) return;
+  const double step = __longlong_as_double((long long)(1023 - beta) << 52);       // 2^-beta
+  const double tail = __longlong_as_double((long long)(1023 - 2 * beta) << 52);   // 2^-2 beta
+  const double ri = rs[i] * tail;
+  for (int j = blockIdx.y; j < N; j += gridDim.y) {
+    const int* sp = S + i + (long)j * M;
+    double t = 0.0;
+    for (int g = G - 1; g >= 0; --g) t = fma(t, step, (double)sp[g * plane]);
+    const double v = t * (ri * cs[j]);
+    double* cp = C + i + (long)j * ldc;
+    *cp = accumulate ? *cp + v : v;
+  }
+}
+
 // Generic digit-split product C (M x N, column-major, ldc) (+)= A B on the
 // tensor cores. Operand descriptions: A rows are K-vectors at A + i*lda
 // (a_rows_strided: A[i + k*lda] instead), B columns are K-vectors at B + j*ldb
@@ -191,7 +229,7 @@ __global__ void __launch_bounds__(256) ozaki_split_rows(const TI* __restrict__ X
 int ozaki_gemm_ex(const OzOperand& A, const OzOperand& B, int M, int N, int K, double* C, long ldc, int s,
                   bool accumulate, void* work, bool split_A, int* status, cudaStream_t st, int s_use) {
   if (M <= 0 || N <= 0) return BSE_OK;
-  if (s < 1 || s * (s + 1) / 2 > tc::kMaxUnits) return BSE_ERR_ARG;
+  if (s < 1 || s > kMaxDigits || s * (s + 1) / 2 > tc::kMaxUnits) return BSE_ERR_ARG;
   if (s_use <= 0 || s_use > s) s_use = s;
   const OzakiPlan p = plan(M, N, K, s);
   char* w = reinterpret_cast<char*>(work);
@@ -227,21 +265,30 @@ int ozaki_gemm_ex(const OzOperand& A, const OzOperand& B, int M, int N, int K, d
   // needs the s_use digits this product pairs
   if (split_A) BSE_TRY(split(A, M, dA, rs, s));
   BSE_TRY(split(B, N, dB, cs, s_use));
-  if (!accumulate) BSE_CUDA(cudaMemset2DAsync(C, ldc * sizeof(double), 0, (size_t)M * sizeof(double), N, st));
+  int* planes = reinterpret_cast<int*>(w + al256o(8 * (size_t)N));
   tc::TcProblem pb{};
   pb.M = M; pb.N = N; pb.K = K; pb.ldk = p.ldk;
   pb.A = dA; pb.B = dB; pb.a_rows = M; pb.b_rows = N; pb.a_digits = s; pb.b_digits = s;
+  pb.chunk_kb = kTcChunkK / 64;
+  // pairs ordered by anti-diagonal d = a + b; the last pair of each closes plane d
   int u = 0;
-  for (int a = 0; a < s_use; ++a)
-    for (int b = 0; a + b < s_use; ++b) {
+  for (int d = 0; d < s_use; ++d)
+    for (int a = 0; a <= d; ++a) {
       pb.a_digit[u] = a;
-      pb.b_digit[u] = b;
-      pb.unit_scale[u] = ldexp(1.0, -p.beta * (a + b + 2));
+      pb.b_digit[u] = d - a;
+      pb.fold[u] = a == d;
       ++u;
     }
   pb.units = u;
-  pb.mode = 1; pb.Cd = C; pb.ldc = ldc; pb.rs = rs; pb.cs = cs; pb.status = status;
-  return tc::tc_gemm(pb, st);
+  pb.mode = 1; pb.Si = planes; pb.plane = (long)M * N; pb.ldc = M; pb.status = status;
+  BSE_TRY(tc::tc_gemm(pb, st));
+  {
+    KprofScope ks(K_ELEMENTWISE, st, 4.0 * s_use * M * (double)N + (accumulate ? 16.0 : 8.0) * M * (double)N, 0.0);
+    const dim3 grid((unsigned)ceil_div(M, 256), (unsigned)(N < 65535 ? N : 65535));
+    ozaki_combine<<<grid, 256, 0, st>>>(M, N, s_use, planes, (long)M * N, rs, cs, p.beta, C, ldc, accumulate ? 1 : 0);
+    BSE_LAUNCH_CHECK();
+  }
+  return BSE_OK;
 }
 
 // C (M x N, column-major, ldc) = A B to FP64 accuracy. work: ozaki_worksize bytes.
@@ -255,9 +302,12 @@ int ozaki_gemm(int M, int N, int K, const double* A, long lda, const double* B, 
 
 extern "C" size_t bse_ozaki_worksize(int M, int N, int K, int s) { return bse::ozaki_worksize(M, N, K, s); }
 
+extern "C" int bse_ozaki_digit_bits(int K) { return K < 1 ? BSE_ERR_ARG : bse::plan(1, 1, K, 1).beta; }
+
 // C (M x N FP64, column-major, ldc) = A B with A K-major (row i at A + i*lda),
 // B column-major (column j at B + j*ldb), to about 5*s bits beyond the row/column
-// scales, on the tensor cores. work: bse_ozaki_worksize(M, N, K, s) bytes.
+// scales (beta = bse_ozaki_digit_bits(K)), on the tensor cores.
+// work: bse_ozaki_worksize(M, N, K, s) bytes.
 extern "C" int bse_ozaki_gemm(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
                               int ldc, int s, void* work, int* dev_status, void* stream) {
   if (M < 1 || N < 1 || K < 1 || !A || !B || !C || lda < K || ldb < K || ldc < M || !work || !dev_status)

@@ -53,7 +53,8 @@ struct RefWork {
   double* Gbig;               // 2n x 2n: [Ur Ui]^T [Rr Ri]
 };
 
-constexpr int kRefineCorrDigits = 5;  // ~25 bits for correction-sized products
+// digits of the correction-sized products: ~25 bits
+static int corr_digits(long m) { return ozaki_digits((int)m, 25); }
 
 // The FP64-accurate M U runs on the tensor cores (digit splitting) from this size on.
 static bool refine_uses_tc(int n) { return 2 * n >= 1024; }
@@ -64,7 +65,7 @@ size_t refine_worksize(int n) {
              al256(64) + al256(64) + al256(4 * (size_t)n) + al256(8 * ((size_t)n / 2 + 2));
   if (refine_uses_tc(n)) {
     b += al256(ozaki_worksize((int)m, 2 * n, (int)m, ozaki_digits((int)m)));
-    b += al256(ozaki_worksize(2 * n, 2 * n, (int)m, kRefineCorrDigits));
+    b += al256(ozaki_worksize(2 * n, 2 * n, (int)m, corr_digits(m)));
     b += al256(8 * (size_t)4 * n * n);
   }
   return b;
@@ -99,7 +100,7 @@ static RefWork carve_ref(void* work, int n) {
   w.Gbig = nullptr;
   if (refine_uses_tc(n)) {
     w.oz = take(ozaki_worksize((int)m, 2 * n, (int)m, ozaki_digits((int)m)));
-    w.oz2 = take(ozaki_worksize(2 * n, 2 * n, (int)m, kRefineCorrDigits));
+    w.oz2 = take(ozaki_worksize(2 * n, 2 * n, (int)m, corr_digits(m)));
     w.Gbig = (double*)take(8 * (size_t)4 * n * n);
   }
   return w;
@@ -663,7 +664,7 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
       // G = [Ur Ui]^T [Rr Ri]; each operand column (an eigenvector, a residual) has a
       // uniform scale, so ~25-bit digits carry these residual-sized products fully
       OzOperand ua{w.Ur, m, false, false}, rb{w.Rrf, m, false, true};
-      BSE_TRY(ozaki_gemm_ex(ua, rb, 2 * n, 2 * n, m, w.Gbig, 2 * n, kRefineCorrDigits, false, w.oz2, true,
+      BSE_TRY(ozaki_gemm_ex(ua, rb, 2 * n, 2 * n, m, w.Gbig, 2 * n, corr_digits(m), false, w.oz2, true,
                             reinterpret_cast<int*>(st), s));
       kcount(1);
       ref_buildE_big<<<eg, 128, 0, s>>>(n, w.Gbig, lam, w.bnorm, w.cid, w.Fa, w.Fb, w.Fc, w.Fd);

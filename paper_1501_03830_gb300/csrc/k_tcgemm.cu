@@ -4,16 +4,23 @@
 //
 // One CTA owns a 128 x 256 output tile and runs a list of "units": unit u
 // multiplies digit matrix a_digit[u] of A by digit matrix b_digit[u] of B over
-// the whole K, accumulating in one of two TMEM accumulators (256 FP32 columns
-// each), while the epilogue drains the other. Both operands are K-major bf16
-// (A: rows x K, B: cols x K, K contiguous), staged by TMA with 128-byte
-// swizzle into a 4-stage shared-memory ring guarded by mbarriers.
+// the whole K. The K range is cut into chunks of chunk_kb 64-deep blocks; each
+// chunk accumulates afresh in one of two TMEM accumulators (256 FP32 columns
+// each) while the threads drain the other into per-thread 32-bit registers.
+// For digit products every chunk sum is an integer of magnitude <= 2^22, so the
+// drain converts it exactly (adding 1.5 * 2^23 puts the integer in the low
+// mantissa bits) and sums in int32: the exact sum over K is not limited by the
+// FP32 accumulator's 24 bits, which lets the digits be wider (fewer of them).
+// Consecutive units flagged as one group (digit pairs on one anti-diagonal
+// p + q = d, which share a scale) share the integer sum, written once per group
+// as an int32 plane; the FP64 scaling and summation of the planes is a separate
+// elementwise pass (k_ozaki.cu). Both operands are K-major bf16 (A: rows x K,
+// B: cols x K, K contiguous), staged by TMA with 128-byte swizzle into a
+// 4-stage shared-memory ring guarded by mbarriers.
 //
-// Warp roles (192 threads): warp 0 = TMA producer, warp 1 = TMEM owner and
-// MMA issuer (one thread), warps 2-5 = epilogue (TMEM lane quadrant = warp % 4).
-// Every mbarrier wait is bounded: on timeout the kernel records
-// BSE_ERR_TIMEOUT, stops issuing work, drains what it issued (bounded again),
-// frees its TMEM and returns.
+// Every probe and wait is bounded: a CTA that sees no progress for kIdleMax
+// probes records BSE_ERR_TIMEOUT, stops issuing work, drains what it issued
+// (bounded again), frees its TMEM and returns.
 #include <cuda.h>
 #include <stdint.h>
 
@@ -32,7 +39,13 @@ constexpr int A_BYTES = BM * BK * 2;  // 16 KiB
 constexpr int B_BYTES = BN * BK * 2;  // 32 KiB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr int THREADS = 192;
+// 8 warps, all of which drain TMEM (lane quadrant = warp % 4, column half =
+// warp / 4); lane 0 of warp 0 also issues the TMA loads and lane 0 of warp 1
+// the MMAs, both by non-blocking mbarrier probes between drains. Eight warps
+// leave each thread up to 255 registers, which the 128 integer sums need.
+constexpr int THREADS = 256;
+constexpr int HALF_N = BN / 2;  // columns per thread
+constexpr long kIdleMax = 1L << 26;  // probes without progress before a CTA gives up
 constexpr uint32_t TMEM_COLS = 512;  // two 128 x 256 FP32 accumulators
 
 using namespace ptx;
@@ -84,7 +97,7 @@ __device__ __forceinline__ void cluster_sync_all() {
 template <int CM, int CN>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const TcParams P) {
+                   const __grid_constant__ TcParams P) {
   constexpr bool MC = CM * CN > 1;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -127,7 +140,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
+      mbar_init(&tempty[b], THREADS);
     }
     mbar_init(drain, 1);
     *err = 0;
@@ -141,108 +154,170 @@ __global__ void __launch_bounds__(THREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  if (warp == 0) {
-    if (lane == 0) {
-      // TMA producer
-      int it = 0;
-      uint32_t issued = 0, last_par = 0;  // per stage: a load was issued / its phase parity
-      for (int u = 0; u < P.units && !*err; ++u) {
-        const int ya = P.a_digit[u] * P.a_rows + m0;
-        const int yb = P.b_digit[u] * P.b_rows + n0;
-        for (int kb = 0; kb < KB; ++kb, ++it) {
-          const int st = it % STAGES;
-          const uint32_t ph = (it / STAGES) & 1;
-          if (!mbar_wait(&empty[st], ph ^ 1, err)) break;
-          uint8_t* sa = smem + st * STAGE_BYTES;
-          mbar_expect_tx(&full[st], STAGE_BYTES);
-          if (CN > 1)
-            tma_load_2d_mc(sa + cj * (A_BYTES / CN), &tmA, kb * BK, ya + cj * (BM / CN), &full[st], row_mask);
-          else
-            tma_load_2d(sa, &tmA, kb * BK, ya, &full[st]);
-          if (CM > 1)
-            tma_load_2d_mc(sa + A_BYTES + ci * (B_BYTES / CM), &tmB, kb * BK, yb + ci * (BN / CM), &full[st],
-                           col_mask);
-          else
-            tma_load_2d(sa + A_BYTES, &tmB, kb * BK, yb, &full[st]);
-          issued |= 1u << st;
-          last_par = (last_par & ~(1u << st)) | (ph << st);
+  const bool producer = warp == 0 && lane == 0;
+  const bool issuer = warp == 1 && lane == 0;
+  // producer state: next K block to load
+  int p_it = 0, p_u = 0, p_kb = 0;
+  uint32_t issued = 0, last_par = 0;  // per stage: a load was issued / its phase parity
+  // MMA state: next K block to multiply, chunk, whether its TMEM buffer is held
+  int m_it = 0, m_u = 0, m_kb = 0, m_ch = 0;
+  bool m_have = false;
+  const uint32_t idesc = make_idesc();
+  // drain state
+  const int q4 = warp & 3;
+  const int cb = (warp >> 2) * HALF_N;
+  const int row = m0 + q4 * 32 + lane;
+  int d_u = 0, d_ch = 0, d_kb0 = 0, nfold = 0;
+  int acc[HALF_N];  // integer sums (mode 1) or FP32 bit patterns (mode 0)
+#pragma unroll
+  for (int j = 0; j < HALF_N; ++j) acc[j] = 0;
+  long idle = 0;
+
+  while (d_u < P.units) {
+    bool progress = false;
+    if (producer) {
+      while (p_u < P.units) {
+        const int st = p_it % STAGES;
+        const uint32_t ph = (p_it / STAGES) & 1;
+        if (!mbar_test(&empty[st], ph ^ 1)) break;
+        const int ya = P.a_digit[p_u] * P.a_rows + m0;
+        const int yb = P.b_digit[p_u] * P.b_rows + n0;
+        uint8_t* sa = smem + st * STAGE_BYTES;
+        mbar_expect_tx(&full[st], STAGE_BYTES);
+        if (CN > 1)
+          tma_load_2d_mc(sa + cj * (A_BYTES / CN), &tmA, p_kb * BK, ya + cj * (BM / CN), &full[st], row_mask);
+        else
+          tma_load_2d(sa, &tmA, p_kb * BK, ya, &full[st]);
+        if (CM > 1)
+          tma_load_2d_mc(sa + A_BYTES + ci * (B_BYTES / CM), &tmB, p_kb * BK, yb + ci * (BN / CM), &full[st],
+                         col_mask);
+        else
+          tma_load_2d(sa + A_BYTES, &tmB, p_kb * BK, yb, &full[st]);
+        issued |= 1u << st;
+        last_par = (last_par & ~(1u << st)) | (ph << st);
+        ++p_it;
+        if (++p_kb == KB) {
+          p_kb = 0;
+          ++p_u;
         }
+        progress = true;
       }
-      // the CTA may leave early after an error: first let every issued copy land
-      for (int st = 0; st < STAGES; ++st)
-        if (issued & (1u << st)) mbar_drain(&full[st], (last_par >> st) & 1);
     }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      // MMA issuer
-      const uint32_t idesc = make_idesc();
-      int it = 0;
-      bool ok = true;
-      for (int u = 0; u < P.units && ok; ++u) {
-        const int buf = u & 1;
-        const uint32_t uph = (u >> 1) & 1;
-        ok = mbar_wait(&tempty[buf], uph ^ 1, err);
-        if (!ok) break;
-        tc_fence_after();
-        const uint32_t d = tmem_base + (uint32_t)(buf * BN);
-        for (int kb = 0; kb < KB; ++kb, ++it) {
-          const int st = it % STAGES;
-          const uint32_t ph = (it / STAGES) & 1;
-          ok = mbar_wait(&full[st], ph, err);
-          if (!ok) break;
+    if (issuer) {
+      // one TMEM accumulator per chunk of chunk_kb K blocks
+      while (m_u < P.units) {
+        const int buf = m_ch & 1;
+        if (!m_have) {
+          if (!mbar_test(&tempty[buf], ((m_ch >> 1) & 1) ^ 1)) break;
           tc_fence_after();
-          const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
-          const uint64_t da = make_desc(sa), db = make_desc(sa + A_BYTES);
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk)
-            umma_bf16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, (kb | kk) != 0);
-          if (MC)
-            umma_commit_mc(&empty[st], (uint16_t)(row_mask | col_mask));
-          else
-            umma_commit(&empty[st]);
+          m_have = true;
         }
-        if (ok) umma_commit(&tfull[buf]);
-      }
-      // all issued MMAs complete before TMEM can be released
-      umma_commit(drain);
-      mbar_drain(drain, 0);
-    }
-  } else {
-    // epilogue: TMEM lane quadrant q4 = warp % 4, one output row per thread
-    const int q4 = warp & 3;
-    const int row = m0 + q4 * 32 + lane;
-    for (int u = 0; u < P.units; ++u) {
-      const int buf = u & 1;
-      const uint32_t uph = (u >> 1) & 1;
-      // warp-uniform wait: tcgen05.ld below needs every lane
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], uph, err));
-      if (!ok) break;
-      tc_fence_after();
-      const uint32_t tb = tmem_base + (uint32_t)(buf * BN) + ((uint32_t)(q4 * 32) << 16);
-      const double ps = P.unit_scale[u];
-      const double rsc = (P.mode == 1 && row < P.M) ? P.rs[row] * ps : 0.0;
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        float v[16];
-        tmem_ld16(tb + (uint32_t)c0, v);
-        if (row < P.M) {
+        const int st = m_it % STAGES;
+        if (!mbar_test(&full[st], (m_it / STAGES) & 1)) break;
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
+        const uint64_t da = make_desc(sa), db = make_desc(sa + A_BYTES);
+        const uint32_t d = tmem_base + (uint32_t)(buf * BN);
+        const int kc = m_kb % P.chunk_kb;
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int col = n0 + c0 + i;
-            if (col < P.N) {
-              if (P.mode == 0) {
-                P.Cf[row + (long)col * P.ldc] = v[i];
-              } else {
-                double* cp = P.Cd + row + (long)col * P.ldc;
-                *cp = fma((double)v[i], rsc * P.cs[col], *cp);
-              }
-            }
-          }
+        for (int kk = 0; kk < BK / 16; ++kk)
+          umma_bf16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, (kc | kk) != 0);
+        if (MC)
+          umma_commit_mc(&empty[st], (uint16_t)(row_mask | col_mask));
+        else
+          umma_commit(&empty[st]);
+        ++m_it;
+        ++m_kb;
+        if (kc == P.chunk_kb - 1 || m_kb == KB) {
+          umma_commit(&tfull[buf]);
+          ++m_ch;
+          m_have = false;
+        }
+        if (m_kb == KB) {
+          m_kb = 0;
+          ++m_u;
+        }
+        progress = true;
+      }
+    }
+    __syncwarp();
+    // drain the next chunk into the per-thread sums (warp-collective TMEM loads)
+    const int buf = d_ch & 1;
+    // every lane probes (each must observe the phase); the phase cannot move on
+    // before this warp has drained it, so a late probe sees the same answer
+    const bool ready = __all_sync(0xffffffffu, mbar_test(&tfull[buf], (d_ch >> 1) & 1));
+    if (ready) {
+      tc_fence_after();
+      const uint32_t tb = tmem_base + (uint32_t)(buf * BN + cb) + ((uint32_t)(q4 * 32) << 16);
+      if (P.mode == 1) {
+#pragma unroll
+        for (int c0 = 0; c0 < HALF_N; c0 += 32) {
+          uint32_t r[32];
+          tmem_ld32(tb + (uint32_t)c0, r);
+          // exact: |chunk sum| <= 2^22, so adding 1.5 * 2^23 leaves it in the low mantissa bits
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            acc[c0 + i] += (int)(__float_as_uint(__uint_as_float(r[i]) + 12582912.0f) - 0x4B400000u);
+        }
+      } else {
+#pragma unroll
+        for (int c0 = 0; c0 < HALF_N; c0 += 32) {
+          uint32_t r[32];
+          tmem_ld32(tb + (uint32_t)c0, r);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[c0 + i] = __float_as_int(__int_as_float(acc[c0 + i]) + __uint_as_float(r[i]));
         }
       }
       tc_fence_before();
       mbar_arrive(&tempty[buf]);
+      ++d_ch;
+      d_kb0 += P.chunk_kb;
+      if (d_kb0 >= KB) {
+        d_kb0 = 0;
+        if (P.fold[d_u]) {
+          // end of a group of units: write the sums (FP32 C, or int32 plane nfold)
+          const int ncols = min(HALF_N, P.N - (n0 + cb));
+          if (row < P.M) {
+            if (P.mode == 0) {
+              float* cp = P.Cf + row + (long)(n0 + cb) * P.ldc;
+#pragma unroll
+              for (int j = 0; j < HALF_N; ++j)
+                if (j < ncols) cp[(long)j * P.ldc] = __int_as_float(acc[j]);
+            } else {
+              int* cp = P.Si + (long)nfold * P.plane + row + (long)(n0 + cb) * P.ldc;
+#pragma unroll
+              for (int j = 0; j < HALF_N; ++j)
+                if (j < ncols) cp[(long)j * P.ldc] = acc[j];
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < HALF_N; ++j) acc[j] = 0;
+          ++nfold;
+        }
+        ++d_u;
+      }
+      progress = true;
     }
+    // bounded: a CTA that sees no progress for kIdleMax probes (or an error
+    // recorded by another warp) stops
+    if (__any_sync(0xffffffffu, progress)) {
+      idle = 0;
+    } else if (++idle > kIdleMax) {
+      *err = BSE_ERR_TIMEOUT;
+    }
+    if (*err) break;
   }
+  if (producer) {
+    // the CTA may leave early after an error: first let every issued copy land
+    for (int st = 0; st < STAGES; ++st)
+      if (issued & (1u << st)) mbar_drain(&full[st], (last_par >> st) & 1);
+  }
+  if (issuer) {
+    // all issued MMAs complete before TMEM can be released
+    umma_commit(drain);
+    mbar_drain(drain, 0);
+  }
+  __syncwarp();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
@@ -306,9 +381,10 @@ static int pair_mode() { return g_pair.load(std::memory_order_relaxed); }
 
 int tc_gemm(const TcProblem& pb, cudaStream_t s) {
   if (pb.M <= 0 || pb.N <= 0 || pb.K <= 0 || pb.units <= 0) return BSE_OK;
-  if (pb.units > kMaxUnits || (pb.ldk % 8) != 0 || (reinterpret_cast<uintptr_t>(pb.A) % 16) != 0 ||
+  if (pb.units > kMaxUnits || pb.chunk_kb < 1 || !pb.fold[pb.units - 1] || (pb.ldk % 8) != 0 ||
+      (reinterpret_cast<uintptr_t>(pb.A) % 16) != 0 ||
       (reinterpret_cast<uintptr_t>(pb.B) % 16) != 0) {
-    record_message("tc_gemm: bad layout (K pitch must be a multiple of 8, bases 16-byte aligned)");
+    record_message("tc_gemm: bad layout (K pitch a multiple of 8, bases 16-byte aligned, chunk >= 1, last unit folds)");
     return BSE_ERR_ARG;
   }
   static std::once_flag attr_once;
@@ -340,12 +416,13 @@ int tc_gemm(const TcProblem& pb, cudaStream_t s) {
   P.M = pb.M; P.N = pb.N; P.K = pb.K;
   P.a_rows = pb.a_rows; P.b_rows = pb.b_rows;
   P.units = pb.units;
+  P.chunk_kb = pb.chunk_kb;
   for (int u = 0; u < pb.units; ++u) {
     P.a_digit[u] = pb.a_digit[u];
     P.b_digit[u] = pb.b_digit[u];
-    P.unit_scale[u] = pb.unit_scale[u];
+    P.fold[u] = pb.fold[u];
   }
-  P.mode = pb.mode; P.Cf = pb.Cf; P.Cd = pb.Cd; P.ldc = pb.ldc; P.rs = pb.rs; P.cs = pb.cs;
+  P.mode = pb.mode; P.Cf = pb.Cf; P.Si = pb.Si; P.plane = pb.plane; P.ldc = pb.ldc;
   P.status = pb.status;
   const long tiles = (long)((pb.M + BM - 1) / BM) * ((pb.N + BN - 1) / BN);
   KprofScope ks(K_GEMM_TC, s, 0.0, 2.0 * pb.M * (double)pb.N * pb.K * pb.units);
@@ -384,7 +461,8 @@ extern "C" int bse_tc_gemm_bf16(int M, int N, int K, const void* A, const void* 
   bse::tc::TcProblem pb{};
   pb.M = M; pb.N = N; pb.K = K; pb.ldk = ldk;
   pb.A = A; pb.B = B; pb.a_rows = M; pb.b_rows = N; pb.a_digits = 1; pb.b_digits = 1;
-  pb.units = 1; pb.a_digit[0] = 0; pb.b_digit[0] = 0; pb.unit_scale[0] = 1.0;
+  pb.units = 1; pb.a_digit[0] = 0; pb.b_digit[0] = 0; pb.fold[0] = 1;
+  pb.chunk_kb = 4;  // FP32 sums of 256-deep chunks: no long in-TMEM accumulation
   pb.mode = 0; pb.Cf = C; pb.ldc = ldc; pb.status = dev_status;
   return bse::tc::tc_gemm(pb, (cudaStream_t)stream);
 }

@@ -13,14 +13,14 @@ struct TcParams {
   int M, N, K;           // output M x N, reduction length K
   int a_rows, b_rows;    // rows per digit matrix in the stacked A / B tensors
   int units;             // digit pairs accumulated by every output tile
+  int chunk_kb;          // K blocks (of 64) per exact accumulation chunk in TMEM
   int a_digit[kMaxUnits], b_digit[kMaxUnits];
-  double unit_scale[kMaxUnits];
-  int mode;              // 0: Cf = acc (FP32); 1: Cd += acc * rs[row] * cs[col] * unit_scale
+  unsigned char fold[kMaxUnits];  // unit u ends a group summed together: write it out
+  int mode;              // 0: Cf = sum (FP32); 1: plane g of Si = integer sum of group g
   float* Cf;
-  double* Cd;
+  int* Si;               // mode 1: int32 planes, M x N column-major (ldc), plane apart
+  long plane;
   long ldc;
-  const double* rs;
-  const double* cs;
   int* status;           // first int of the caller's status word (nullable)
 };
 
@@ -32,14 +32,14 @@ struct TcProblem {
   const void* B;
   int a_rows, b_rows, a_digits, b_digits;
   int units;
+  int chunk_kb;
   int a_digit[kMaxUnits], b_digit[kMaxUnits];
-  double unit_scale[kMaxUnits];
+  unsigned char fold[kMaxUnits];
   int mode;
   float* Cf;
-  double* Cd;
+  int* Si;
+  long plane;
   long ldc;
-  const double* rs;
-  const double* cs;
   int* status;
 };
 

@@ -1,7 +1,7 @@
 """Time one kernel family of the solver in isolation, on synthetic device data.
 
     python -m paper_1501_03830_gb300.stagebench tc32 --M 4096 --N 4096 --K 4096
-    python -m paper_1501_03830_gb300.stagebench ozaki --M 4096 --N 4096 --K 16384 --s 10
+    python -m paper_1501_03830_gb300.stagebench ozaki --M 4096 --N 4096 --K 16384 --s 8
     python -m paper_1501_03830_gb300.stagebench tridiag --m 8192 [--fp64]
     python -m paper_1501_03830_gb300.stagebench tdeig --m 16384
 
@@ -38,7 +38,7 @@ def run(argv=None) -> dict:
     ap.add_argument("--M", type=int, default=4096)
     ap.add_argument("--N", type=int, default=4096)
     ap.add_argument("--K", type=int, default=4096)
-    ap.add_argument("--s", type=int, default=10, help="digits per operand (ozaki)")
+    ap.add_argument("--s", type=int, default=8, help="digits per operand (ozaki)")
     ap.add_argument("--split", type=int, default=1, help="tc32: 1 = 3xTF32, 0 = one TF32 pass")
     ap.add_argument("--m", type=int, default=8192, help="matrix order (tridiag, tdeig)")
     ap.add_argument("--fp64", action="store_true", help="tridiag in FP64 instead of FP32")

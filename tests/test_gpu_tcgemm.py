@@ -1,8 +1,10 @@
 """The tcgen05 tensor-core GEMM and the FP64-accurate digit-split product built on it.
 
 The digit product relies on the tensor cores accumulating integer-valued bf16
-products exactly in FP32 (every partial sum is an integer below 2^24); the first
-test checks exactly that against an FP64 product of the same integers.
+products exactly in FP32 (every partial sum of a 256-deep chunk is an integer
+below 2^22); the first test checks exactness against an FP64 product of the same
+integers, and the integer-input digit-product test checks the whole chain
+(digits, chunk sums, int32 anti-diagonal planes, FP64 combination) exactly.
 """
 import numpy as np
 import pytest
@@ -80,11 +82,39 @@ def test_ozaki_fp64_accuracy(M, N, K, s):
     got = C.cpu().numpy().T
     ref = A @ B
     scale = np.abs(A) @ np.abs(B)
-    beta = (24 - int(np.ceil(np.log2((K + 63) // 64 * 64)))) // 2
+    beta = L.bse_ozaki_digit_bits(K)
+    assert beta == (7 if K >= 256 else beta)
     bound = 8.0 * 2.0 ** (-beta * s) * np.max(np.abs(A)) * np.max(np.abs(B)) * K
     assert np.max(np.abs(got - ref)) <= max(bound, 4e-16 * np.max(scale))
     # FP64-level: far below what FP32 accumulation gives
     assert np.max(np.abs(got - ref) / scale) <= 1e-12
+
+
+@pytest.mark.parametrize("M,N,K", [(384, 512, 4096), (512, 512, 1000), (256, 768, 16384)])
+def test_ozaki_exact_on_integer_inputs(M, N, K):
+    """Integer entries below 2^13 split into two 7-bit digits, so s = 3 digit
+    pairs (p + q < 3) cover every nonzero digit product; all sums are integers
+    below 2^53, so the result must equal the integer product exactly. Row
+    magnitudes vary (rows scaled down by powers of two) so the per-row digit
+    scales differ."""
+    torch = torch_cuda()
+    L, bse = _lib()
+    rng = np.random.default_rng(M + N + K)
+    A = rng.integers(-(2 ** 13) + 1, 2 ** 13, size=(M, K)).astype(np.float64)
+    A = np.trunc(A / (2.0 ** (np.arange(M) % 9))[:, None])
+    B = rng.integers(-(2 ** 13) + 1, 2 ** 13, size=(K, N)).astype(np.float64)
+    Ad = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    Bd = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    s = 3
+    C = torch.full((N, M), np.nan, dtype=torch.float64, device="cuda")
+    work = torch.empty(L.bse_ozaki_worksize(M, N, K, s), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")
+    bse.check(L.bse_ozaki_gemm(M, N, K, Ad.data_ptr(), K, Bd.data_ptr(), K, C.data_ptr(), M, s, work.data_ptr(),
+                               st.data_ptr(), None), "ozaki")
+    torch.cuda.synchronize()
+    assert int(st[0].item()) == 0
+    ref = A @ B  # exact: |entries| < 2^13 * 2^13 * K < 2^53
+    assert np.array_equal(C.cpu().numpy().T, ref)
 
 
 # ---- FP32 GEMM on the tensor cores (3xTF32) ---------------------------------
@@ -194,7 +224,7 @@ def test_ozaki_cta_pairs_same_result(M, N, K, s):
             assert int(st[0].item()) == 0
             out.append(C.t().clone())
     finally:
-        L.bse_set_tc_pairs(2)
+        L.bse_set_tc_pairs(1)
     assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
     ref = A @ B.t()
     scale = A.abs().max(dim=1).values[:, None] * B.abs().max(dim=1).values[None, :] * K ** 0.5

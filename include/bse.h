@@ -116,6 +116,21 @@ int bse_solve(bse_ctx* ctx, int n, const double* A, int lda, const double* B, in
 int bse_spectrum(bse_ctx* ctx, const bse_sol* sol, const double* d_r, const double* d_l,
                  double* w);
 
+/* Spectral density (Eq. DOS) and optical absorption spectrum (Eq. absp) of a
+ * kept solution on a grid of energies, with the delta function replaced by the
+ * Gaussian exp(-t^2/(2 sigma^2)) / (sqrt(2 pi) sigma) (Section 5):
+ *   dos[k] = 1/(2n) sum_j [g(omega_k - lambda_j) + g(omega_k + lambda_j)]
+ *            (all 2n eigenvalues +-lambda_j of H, Theorem 1)
+ *   eps[k] = sum_j w_j g(omega_k - lambda_j), w_j the Eq. absp weights
+ *   omega     n_omega energies (host or device)
+ *   sigma     > 0
+ *   d_r, d_l  2n complex128 dipole vectors, or both NULL (then eps must be NULL)
+ *   dos       out: n_omega doubles (host or device)
+ *   eps       out (nullable): n_omega complex128 (host or device)
+ * Blocks until the outputs are written. Errors: BSE_ERR_ARG, BSE_ERR_CUDA. */
+int bse_absorption(bse_ctx* ctx, const bse_sol* sol, const double* d_r, const double* d_l, int n_omega,
+                   const double* omega, double sigma, double* dos, double* eps);
+
 /* Size n and device pointers of a kept solution (lambda: n doubles; X: 2n x n
  * complex128, ld 2n). The pointers stay owned by the solution. */
 int bse_sol_view(const bse_sol* sol, int* n, const double** lambda_dev, const double** X_dev);

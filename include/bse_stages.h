@@ -121,6 +121,15 @@ size_t bse_stage_refine_worksize(int n);
 int bse_stage_refine(int n, const double* M, double* lam, double* X, int max_sweeps, void* work, int* dev_status,
                      void* stream, int* sweeps, double* diag3);
 
+/* Gaussian-broadened spectral density and absorption spectrum (Eq. DOS, Eq. absp,
+ * Section 5's Gaussian of standard deviation sigma > 0), device pointers:
+ * lambda: n positive eigenvalues; w: n complex128 weights (nullable when eps is
+ * NULL); omega: n_omega grid energies; dos: n_omega out; eps: n_omega complex128
+ * out (nullable). Sums over every eigenvalue (terms below the FP64 range are
+ * exact zeros and skipped). */
+int bse_stage_broaden(int n, const double* lambda, const double* w, int n_omega, const double* omega, double sigma,
+                      double* dos, double* eps, void* stream);
+
 /* ---- tensor-core products (no counterpart in the paper: the FP64-accurate residual
  * of the refinement runs on the bf16 tensor cores) ---------------------------- */
 

@@ -11,6 +11,10 @@ What is computed, and where the paper defines it:
 * the positive eigenvalues lambda_1..lambda_n, right eigenvectors x_j,
   left eigenvectors y_j = S x_j with y_j^H x_j = 1           (Theorem 3)
 * absorption weights (d_r^H x_j)(y_j^H d_l)/(y_j^H x_j)      (Eq. absp)
+* the spectral density over all 2n eigenvalues (Eq. DOS) and the absorption
+  spectrum (Eq. absp), with the delta function replaced by Section 5's
+  Gaussian of standard deviation sigma
+* the Tamm-Dancoff eigenvalues: those of A alone (B = 0)     (Section 2, Thm TDA)
 * the accuracy metrics of Table 1.
 
 Route: Omega = Lc Lc^H (Cholesky), C = Lc^{-1} S Lc^{-H} is Hermitian with
@@ -120,6 +124,31 @@ def weights(X: np.ndarray, Y: np.ndarray, d_r: np.ndarray, d_l: np.ndarray) -> n
     b = Y.conj().T @ d_l
     c = np.einsum("ij,ij->j", Y.conj(), X)
     return a * b / c
+
+
+def gaussian_delta(t, sigma: float):
+    """Section 5: delta(t) ~ exp(-t^2 / (2 sigma^2)) / (sqrt(2 pi) sigma)."""
+    t = np.asarray(t, dtype=np.float64)
+    return np.exp(-(t * t) / (2.0 * sigma * sigma)) / (np.sqrt(2.0 * np.pi) * sigma)
+
+
+def dos(lam: np.ndarray, omega: np.ndarray, sigma: float) -> np.ndarray:
+    """Eq. DOS: phi(omega) = 1/(2n) sum over the 2n eigenvalues of H, which are
+    +-lambda_j (Theorem 1), of delta(omega - lambda)."""
+    eigs = np.concatenate([lam, -lam])
+    return gaussian_delta(omega[:, None] - eigs[None, :], sigma).sum(axis=1) / eigs.shape[0]
+
+
+def absorption(lam: np.ndarray, w: np.ndarray, omega: np.ndarray, sigma: float) -> np.ndarray:
+    """Eq. absp: eps+(omega) = sum_j w_j delta(omega - lambda_j) over the positive half."""
+    return (w[None, :] * gaussian_delta(omega[:, None] - lam[None, :], sigma)).sum(axis=1)
+
+
+def tda_eigenvalues(A: np.ndarray) -> np.ndarray:
+    """Tamm-Dancoff approximation: B dropped, the eigenvalues of the Hermitian A
+    (library eigvalsh as the step), ascending."""
+    Af, _ = symmetrize_lower(A, np.zeros_like(A))
+    return np.linalg.eigvalsh(Af)
 
 
 def negative_half(X: np.ndarray) -> np.ndarray:

@@ -37,12 +37,13 @@ STAGE_NAMES = ["form_M", "cholesky", "form_W", "tridiag", "tdeig", "backtransfor
 
 # Every symbol the headers declare (checked by the CPU test suite).
 EXPORTS = [
-    "bse_create", "bse_destroy", "bse_set_stream", "bse_set_timing", "bse_solve", "bse_spectrum", "bse_sol_view",
+    "bse_create", "bse_destroy", "bse_set_stream", "bse_set_timing", "bse_solve", "bse_spectrum", "bse_absorption",
+    "bse_sol_view",
     "bse_sol_free", "bse_serve_start", "bse_submit", "bse_poll", "bse_serve_stop", "bse_solve_batched",
     "bse_last_error", "bse_version", "bse_launch_count", "bse_kprof_enable", "bse_kprof_read",
     "bse_stage_form_M", "bse_stage_potrf_worksize", "bse_stage_potrf", "bse_stage_form_W",
     "bse_stage_tridiag_worksize", "bse_stage_tridiag", "bse_debug_trace_tridiag", "bse_stage_tridiag_grid", "bse_stage_tdeig_worksize", "bse_stage_tdeig", "bse_stage_tdeig_noalloc",
-    "bse_stage_backtransform_worksize", "bse_stage_backtransform", "bse_stage_weights",
+    "bse_stage_backtransform_worksize", "bse_stage_backtransform", "bse_stage_weights", "bse_stage_broaden",
     "bse_stage_refine_worksize", "bse_stage_refine", "bse_tc_gemm_bf16", "bse_ozaki_worksize", "bse_ozaki_gemm",
     "bse_ozaki_digit_bits",
     "bse_tc32_gemm", "bse_set_fp32_gemm", "bse_set_tc_pairs",
@@ -96,6 +97,7 @@ def lib() -> C.CDLL:
         "bse_set_timing": (i, [vp, i]),
         "bse_solve": (i, [vp, i, vp, i, vp, i, i, vp, vp, vp, C.POINTER(vp), C.POINTER(bse_info)]),
         "bse_spectrum": (i, [vp, vp, vp, vp, vp]),
+        "bse_absorption": (i, [vp, vp, vp, vp, i, vp, C.c_double, vp, vp]),
         "bse_sol_view": (i, [vp, C.POINTER(i), C.POINTER(vp), C.POINTER(vp)]),
         "bse_sol_free": (i, [vp]),
         "bse_serve_start": (i, [vp, i]),
@@ -122,6 +124,7 @@ def lib() -> C.CDLL:
         "bse_stage_backtransform_worksize": (sz, [i, i]),
         "bse_stage_backtransform": (i, [i, vp, i, vp, i, vp, vp, vp, vp, vp, i, i, vp, vp]),
         "bse_stage_weights": (i, [i, vp, i, vp, vp, vp, vp]),
+        "bse_stage_broaden": (i, [i, vp, vp, i, vp, C.c_double, vp, vp, vp]),
         "bse_stage_refine_worksize": (sz, [i]),
         "bse_stage_refine": (i, [i, vp, vp, vp, i, vp, vp, vp, C.POINTER(i), C.POINTER(d)]),
         "bse_tc_gemm_bf16": (i, [i, i, i, vp, vp, i, vp, i, vp, vp]),
@@ -263,6 +266,26 @@ class Context:
         w = out if out is not None else np.empty(n, dtype=np.complex128)
         check(lib().bse_spectrum(self.handle, sol.handle, ptr(d_r), ptr(d_l), ptr(w)), "bse_spectrum")
         return w
+
+    def absorption(self, sol: Solution, omega, sigma: float, d_r=None, d_l=None, out=None):
+        """bse_absorption: Gaussian-broadened spectral density (Eq. DOS) and, with
+        dipoles, absorption spectrum (Eq. absp) on the grid ``omega``. Returns
+        (dos, eps) with eps None without dipoles; numpy in, numpy out unless
+        ``out`` = (dos, eps) device buffers are given."""
+        if isinstance(omega, np.ndarray):
+            omega = np.ascontiguousarray(omega, dtype=np.float64)
+        if isinstance(d_r, np.ndarray):
+            d_r = np.ascontiguousarray(d_r, dtype=np.complex128)
+            d_l = np.ascontiguousarray(d_l, dtype=np.complex128)
+        k = len(omega)
+        if out is not None:
+            dos, eps = out
+        else:
+            dos = np.empty(k, dtype=np.float64)
+            eps = np.empty(k, dtype=np.complex128) if d_r is not None else None
+        check(lib().bse_absorption(self.handle, sol.handle, ptr(d_r), ptr(d_l), k, ptr(omega), float(sigma), ptr(dos),
+                                   ptr(eps)), "bse_absorption")
+        return dos, eps
 
     def solve_batched(self, problems, precision="mixed_refined", want_X=True, outs=None):
         """bse_solve_batched over a list of (A, B) pairs (numpy host arrays or

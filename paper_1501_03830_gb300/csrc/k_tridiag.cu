@@ -42,7 +42,8 @@ struct TrdWork {
   T* Dpart;     // direct partials   [ns][maxQ][32] (maxQ <= ns)
   T* Tpart;     // transposed partials [ns][ns][32]
   double* normpart;  // [kMaxGrid] per-block partial squared norms of the next column
-  double* dotpart;   // [kMaxGrid][2NB] per-block partial V^T v, P^T v
+  double* dotpart;   // [2][kMaxGrid][2NB] per-block partial V^T w, P^T w (by column parity)
+  double* dotpart2;  // [kMaxGrid / 8][2NB] sums of 8 blocks' partials
   unsigned* bar;     // grid barrier words
 };
 
@@ -61,7 +62,8 @@ size_t trd_worksize(int m) {
   b += align256(sizeof(T) * ns * maxQ * TRD_TB);
   b += align256(sizeof(T) * ns * ns * TRD_TB);
   b += align256(sizeof(double) * kMaxGrid);
-  b += align256(sizeof(double) * kMaxGrid * 2 * TRD_NB);
+  b += align256(sizeof(double) * 2 * kMaxGrid * 2 * TRD_NB);
+  b += align256(sizeof(double) * (kMaxGrid / 8) * 2 * TRD_NB);
   b += align256(64);
   return b;
 }
@@ -77,7 +79,8 @@ static TrdWork<T> carve(void* work, int m) {
   w.Dpart = reinterpret_cast<T*>(p); p += align256(sizeof(T) * ns * maxQ * TRD_TB);
   w.Tpart = reinterpret_cast<T*>(p); p += align256(sizeof(T) * ns * ns * TRD_TB);
   w.normpart = reinterpret_cast<double*>(p); p += align256(sizeof(double) * kMaxGrid);
-  w.dotpart = reinterpret_cast<double*>(p); p += align256(sizeof(double) * kMaxGrid * 2 * TRD_NB);
+  w.dotpart = reinterpret_cast<double*>(p); p += align256(sizeof(double) * 2 * kMaxGrid * 2 * TRD_NB);
+  w.dotpart2 = reinterpret_cast<double*>(p); p += align256(sizeof(double) * (kMaxGrid / 8) * 2 * TRD_NB);
   w.bar = reinterpret_cast<unsigned*>(p);
   return w;
 }
@@ -111,6 +114,7 @@ struct PanelArgs {
   T* Tpart;
   double* normpart;
   double* dotpart;
+  double* dotpart2;
   double* e;
   T* tau;
   unsigned* bar;  // [0] arrivals, [1] generation
@@ -375,6 +379,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
   __shared__ double red8[8];
   __shared__ double dred[8][2 * TRD_NB];
+  __shared__ T wdots[8][2 * TRD_NB];
   const int m = a.m;
   const long ldw = a.ldw;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -416,37 +421,16 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
       a.e[j] = h.beta;
       a.tau[j] = (T)h.tau;
     }
-    const int r_own = s + blockIdx.x * 256 + tid;
-    // panel dot products over the owned rows
-    if (c > 0 && blockIdx.x * 256 + s < m) {
-      // in the path's own precision: FP64 arithmetic is a small fraction of the
-      // FP32 rate on this GPU and would dominate the column on the FP32 path
-      T vr = T(0);
-      if (r_own < m) vr = (r_own == s) ? T(1) : ldcg(W + r_own + (long)j * ldw) * scal;
-      T* tred = reinterpret_cast<T*>(&dred[0][0]);  // [8][2NB] in T
-      const int nq2 = 2 * c;
-      for (int q0 = 0; q0 < nq2; q0 += 32) {
-        T acc[32];
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const int q = q0 + k;
-          T pv = T(0);
-          if (q < nq2 && r_own < m) {
-            const int col = q < c ? q : TRD_NB + (q - c);
-            pv = ldcg(VP + r_own + (long)col * ldvp) * vr;
-          }
-          acc[k] = pv;
-        }
-        warp_reduce_scatter32<T>(acc, lane);
-        if (q0 + lane < nq2) tred[wid * 2 * TRD_NB + q0 + lane] = acc[0];
-      }
-      __syncthreads();
-      for (int q = tid; q < nq2; q += 256) {
-        T t = T(0);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) t += tred[k * 2 * TRD_NB + q];
+    // first level of the dot-product reduction: block b < grid/8 adds the partials
+    // of blocks 8b .. 8b+7 (written by the previous column's phase D)
+    if (c > 0 && blockIdx.x * 8 < gridDim.x) {
+      const double* d1 = a.dotpart + (long)(c & 1) * kMaxGrid * 2 * TRD_NB;
+      const int b0 = blockIdx.x * 8, b1 = min(b0 + 8, (int)gridDim.x);
+      for (int q = tid; q < 2 * c; q += 256) {
         const int slot = q < c ? q : TRD_NB + (q - c);
-        a.dotpart[(long)blockIdx.x * 2 * TRD_NB + slot] = (double)t;
+        T t = T(0);
+        for (int b = b0; b < b1; ++b) t += (T)ldcg(d1 + (long)b * 2 * TRD_NB + slot);
+        a.dotpart2[(long)blockIdx.x * 2 * TRD_NB + slot] = (double)t;
       }
     }
     trace_point(a, j, 2);
@@ -473,7 +457,6 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
       const int ns = ceil_div(m, TRD_TB) - sb;
       const int qc = symv_qc(ns, nwarps);
       const int maxQ = (ns + qc - 1) / qc;
-      const int nrb = (m - s + 255) / 256;  // blocks that own rows (and wrote dot partials)
       const T tauj = (T)h.tau;
       const bool next = (c + 1 < a.nbp);
       // the panel's small vectors, staged once per block: V^T v, P^T v and row s of V, P
@@ -481,37 +464,48 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
       T* sdP = sdV + TRD_NB;
       T* sVs = sdP + TRD_NB;
       T* sPs = sVs + TRD_NB;
-      // each dot product: sum of nrb block partials, 8 lanes per dot product
+      // V^T v and P^T v: v = scal * w below row s and v[s] = 1, so each is row s of
+      // V (P) plus scal times the dot products with w that the previous column's
+      // phase D accumulated over rows > s (per-block partials, parity c & 1, summed
+      // 8 blocks at a time in phase B/C, the rest here)
+      const double* dpart = a.dotpart2;
+      const int nblk = ceil_div((int)gridDim.x, 8);
       for (int q0 = wid * 4; q0 < 2 * c; q0 += 32) {
         const int q = q0 + (lane >> 3), l8d = lane & 7;
         T acc = T(0);
+        int slot = 0;
         if (q < 2 * c) {
-          const int slot = q < c ? q : TRD_NB + (q - c);
+          slot = q < c ? q : TRD_NB + (q - c);
           // independent partial sums so the loads are all in flight at once
           T pa[8];
 #pragma unroll
           for (int k = 0; k < 8; ++k) pa[k] = T(0);
           int b = l8d;
-          for (; b + 56 < nrb; b += 64) {
+          for (; b + 56 < nblk; b += 64) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) pa[k] += (T)ldcg(a.dotpart + (long)(b + 8 * k) * 2 * TRD_NB + slot);
+            for (int k = 0; k < 8; ++k) pa[k] += (T)ldcg(dpart + (long)(b + 8 * k) * 2 * TRD_NB + slot);
           }
 #pragma unroll
           for (int k = 0; k < 8; ++k)
-            if (b + 8 * k < nrb) pa[k] += (T)ldcg(a.dotpart + (long)(b + 8 * k) * 2 * TRD_NB + slot);
+            if (b + 8 * k < nblk) pa[k] += (T)ldcg(dpart + (long)(b + 8 * k) * 2 * TRD_NB + slot);
           acc = ((pa[0] + pa[1]) + (pa[2] + pa[3])) + ((pa[4] + pa[5]) + (pa[6] + pa[7]));
         }
 #pragma unroll
         for (int o = 4; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (q < 2 * c && l8d == 0) {
-          if (q < c) sdV[q] = acc;
-          else sdP[q - c] = acc;
+          const T lead = ldcg(VP + s + (long)slot * ldvp);
+          const T d = fma(scal, acc, lead);
+          if (q < c) sdV[q] = d;
+          else sdP[q - c] = d;
         }
       }
       for (int t = tid; t < c; t += 256) {
         sVs[t] = ldcg(VP + s + (long)t * ldvp);
         sPs[t] = ldcg(VP + s + (long)(TRD_NB + t) * ldvp);
       }
+      // this warp's partial dot products of the next column with V, P (t <= c)
+      T* wd = &wdots[wid][0];
+      for (int t = lane; t < 2 * TRD_NB; t += 32) wd[t] = T(0);
       __syncthreads();
       // p at row s (= j+1): every block needs it for the next column's update
       T p_s = T(0);
@@ -554,6 +548,16 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
         const int Rr = r / TRD_TB - sbD, l = r % TRD_TB;
         const int nq = valid ? Rr / qc + 1 : 0;
         const int nsv = valid ? ns : 0;
+        // the row's panel entries V[r, t], P[r, t] (t = l8 + 8k < c), loaded up front
+        // so their latency overlaps the partial-sum loads below
+        T vvk[8], ppk[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int t = l8 + 8 * k;
+          const bool ok = valid && t < c;
+          vvk[k] = ok ? ldcg(VP + r + (long)t * ldvp) : T(0);
+          ppk[k] = ok ? ldcg(VP + r + (long)(TRD_NB + t) * ldvp) : T(0);
+        }
         T acc[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc[k] = T(0);
@@ -570,39 +574,76 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
         const bool upd = next && r >= s + 1;
         const int j1 = j + 1;
         T w = T(0);
-        for (int t = l8; valid && t < c; t += 8) {
-          const T vv = ldcg(VP + r + (long)t * ldvp), pp = ldcg(VP + r + (long)(TRD_NB + t) * ldvp);
-          y = fma(vv, sdP[t], y);
-          y = fma(-pp, sdV[t], y);
-          w = fma(vv, sPs[t], w);
-          w = fma(-pp, sVs[t], w);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int t = l8 + 8 * k;
+          if (valid && t < c) {
+            y = fma(vvk[k], sdP[t], y);
+            y = fma(-ppk[k], sdV[t], y);
+            w = fma(vvk[k], sPs[t], w);
+            w = fma(-ppk[k], sVs[t], w);
+          }
         }
 #pragma unroll
         for (int o = 4; o >= 1; o >>= 1) {
           y += __shfl_xor_sync(0xffffffffu, y, o);
           w += __shfl_xor_sync(0xffffffffu, w, o);
         }
+        // every lane of the row's group finishes the row (the sums are replicated by
+        // the butterfly); lane l8 == 0 stores
+        const T vr = !valid ? T(0) : (r == s) ? T(1) : ldcg(W + r + (long)j * ldw) * scal;
+        const T p = tauj * y;
+        T wf = T(0);
+        if (valid && upd) {
+          // column j+1 with all panel terms t <= c; t = c: V[j1, c] = 1, P[j1, c] = p_s
+          w += ldcg(W + r + (long)j1 * ldw);
+          w = fma(vr, p_s, w);
+          w = fma(-p, T(1), w);
+          wf = w;
+        }
         if (valid && l8 == 0) {
-          const T vr = (r == s) ? T(1) : ldcg(W + r + (long)j * ldw) * scal;
-          const T p = tauj * y;
           VP[r + (long)c * ldvp] = vr;
           VP[r + (long)(TRD_NB + c) * ldvp] = p;
           PV[r + (long)c * ldvp] = p;
           PV[r + (long)(TRD_NB + c) * ldvp] = -vr;
           W[r + (long)j * ldw] = vr;  // the reflector, leading 1 included
           if (upd) {
-            // column j+1 with all panel terms t <= c; t = c: V[j1, c] = 1, P[j1, c] = p_s
-            w += W[r + (long)j1 * ldw];
-            w = fma(vr, p_s, w);
-            w = fma(-p, T(1), w);
-            W[r + (long)j1 * ldw] = w;
-            if (r >= j1 + 2) sq += (double)w * (double)w;
+            W[r + (long)j1 * ldw] = wf;
+            if (r >= j1 + 2) sq += (double)wf * (double)wf;
+          }
+        }
+        if (next) {
+          // next column's dot products with the panel, rows below its leading entry:
+          // lane l8 takes t = l8 + 8k (t < c from the prefetched entries, t = c the
+          // new column v, p); the 4 rows of the warp are summed by shuffles
+          const T wd_r = (valid && upd && r >= j1 + 2) ? wf : T(0);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int t = l8 + 8 * k;
+            T dv = (t < c ? vvk[k] : (t == c ? vr : T(0))) * wd_r;
+            T dq = (t < c ? ppk[k] : (t == c ? p : T(0))) * wd_r;
+            dv += __shfl_xor_sync(0xffffffffu, dv, 8);
+            dq += __shfl_xor_sync(0xffffffffu, dq, 8);
+            dv += __shfl_xor_sync(0xffffffffu, dv, 16);
+            dq += __shfl_xor_sync(0xffffffffu, dq, 16);
+            if (lane < 8 && t <= c) {
+              wd[t] += dv;
+              wd[TRD_NB + t] += dq;
+            }
           }
         }
       }
       if (next) {
-        sq = block_sum<T>(sq, red8);
+        sq = block_sum<T>(sq, red8);  // also orders the warps' dot partials before their sum
         if (tid == 0) a.normpart[blockIdx.x] = sq;
+        double* dnext = a.dotpart + (long)((c + 1) & 1) * kMaxGrid * 2 * TRD_NB + (long)blockIdx.x * 2 * TRD_NB;
+        for (int q = tid; q < 2 * (c + 1); q += 256) {
+          const int slot = q <= c ? q : TRD_NB + (q - c - 1);
+          T t = T(0);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) t += wdots[k][slot];
+          dnext[slot] = (double)t;
+        }
       }
       __syncthreads();  // the staged vectors are rewritten for the next column
     }
@@ -825,7 +866,8 @@ int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStr
     const int grid = (int)max(1L, min((long)nsm * per_sm, want));
     PanelArgs<T> pa;
     pa.m = m; pa.j0 = j0; pa.nbp = nbp; pa.W = W; pa.ldw = ldw; pa.VP = w.VP; pa.PV = w.PV; pa.ldvp = ldvp;
-    pa.Dpart = w.Dpart; pa.Tpart = w.Tpart; pa.normpart = w.normpart; pa.dotpart = w.dotpart; pa.e = e; pa.tau = tau;
+    pa.Dpart = w.Dpart; pa.Tpart = w.Tpart; pa.normpart = w.normpart;
+    pa.dotpart = w.dotpart; pa.dotpart2 = w.dotpart2; pa.e = e; pa.tau = tau;
     pa.bar = w.bar; pa.st = status;
     pa.vec = ((ldw * (long)sizeof(T)) % 16 == 0) && ((reinterpret_cast<uintptr_t>(W) % 16) == 0);
     pa.trace = g_trace;

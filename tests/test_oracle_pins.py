@@ -251,6 +251,71 @@ def test_alg1_minus_iW_spectrum():
     assert _rel(-ev[:n][::-1], s.lam) <= 1e-13
 
 
+# --- spectra (Eq. DOS, Eq. absp, Section 5's Gaussian) -----------------------
+
+
+def test_gaussian_delta_closed_forms():
+    """Section 5's Gaussian: peak 1/(sqrt(2 pi) sigma), unit integral, half
+    maximum at t = sigma sqrt(2 ln 2)."""
+    sig = 5e-4
+    assert abs(D.gaussian_delta(0.0, sig) - 1.0 / (np.sqrt(2 * np.pi) * sig)) <= 1e-12 / sig
+    t = np.linspace(-12 * sig, 12 * sig, 48001)
+    assert abs(np.trapezoid(D.gaussian_delta(t, sig), t) - 1.0) <= 1e-12
+    half = sig * np.sqrt(2 * np.log(2))
+    assert abs(D.gaussian_delta(half, sig) / D.gaussian_delta(0.0, sig) - 0.5) <= 1e-14
+
+
+def test_dos_normalization_symmetry_and_peaks():
+    """Eq. DOS counts all 2n eigenvalues +-lambda_j with weight 1/(2n): the density
+    integrates to 1 over the real line, is even in omega, and an isolated
+    eigenvalue gives a peak of height g(0)/(2n)."""
+    lam = np.array([1.0, 1.7, 2.9])
+    sig = 0.01
+    om = np.linspace(-3.5, 3.5, 140001)
+    phi = D.dos(lam, om, sig)
+    assert abs(np.trapezoid(phi, om) - 1.0) <= 1e-10
+    assert np.allclose(phi, phi[::-1], rtol=0, atol=1e-12 * phi.max())
+    peak = D.dos(lam, np.array([1.7]), sig)[0]
+    assert abs(peak - D.gaussian_delta(0.0, sig) / 6.0) <= 1e-12 * peak
+
+
+@pytest.mark.parametrize("n,seed", [(3, 1), (6, 2)])
+def test_absorption_sum_rule(n, seed):
+    """Completeness of the biorthonormal pairs (Theorem 3, Y^H X = I over all 2n):
+    sum over +-lambda of (d_r^H x)(y^H d_l) = d_r^H d_l. The broadened spectra of
+    both halves therefore integrate to d_r^H d_l, and the positive half alone to
+    sum_j w_j (Eq. absp, unit-integral Gaussians)."""
+    p = make_problem(n, seed)
+    s = D.solve(p.A, p.B)
+    rng = np.random.default_rng(seed)
+    dr = rng.standard_normal(2 * n) + 1j * rng.standard_normal(2 * n)
+    dl = rng.standard_normal(2 * n) + 1j * rng.standard_normal(2 * n)
+    lf, Xf, Yf = D.full_pairs(s.lam, s.X)
+    wf = D.weights(Xf, Yf, dr, dl)
+    assert abs(wf.sum() - dr.conj() @ dl) <= 1e-12 * np.linalg.norm(dr) * np.linalg.norm(dl)
+    w = D.weights(s.X, s.Y, dr, dl)
+    sig = 0.02
+    om = np.linspace(0.0, s.lam.max() + 12 * sig, 200001)
+    eps = D.absorption(s.lam, w, om, sig)
+    assert abs(np.trapezoid(eps, om) - w.sum()) <= 1e-9 * np.abs(w).sum()
+    om2 = np.linspace(-s.lam.max() - 12 * sig, s.lam.max() + 12 * sig, 400001)
+    both = D.absorption(lf, wf, om2, sig)
+    assert abs(np.trapezoid(both, om2) - dr.conj() @ dl) <= 1e-9 * np.abs(wf).sum()
+
+
+@pytest.mark.parametrize("n,seed", [(5, 3), (12, 4)])
+def test_tda_eigenvalues(n, seed):
+    """B = 0 makes H block diagonal (Eq. 1): its positive eigenvalues are those of
+    A exactly, the Tamm-Dancoff values; with B != 0 every lambda_j(H) lies below
+    lambda_j(A) (Theorem TDA)."""
+    p = make_problem(n, seed)
+    tda = D.tda_eigenvalues(p.A)
+    s0 = D.solve(p.A, np.zeros_like(p.B))
+    assert _rel(s0.lam, tda) <= 1e-13
+    s = D.solve(p.A, p.B)
+    assert np.all(s.lam <= tda * (1 + 1e-14))
+
+
 # --- planted mistakes: each must be caught by a pin -----------------------------
 
 
@@ -302,3 +367,15 @@ def test_planted_mistake_normalization_is_caught():
     Xf = np.concatenate([s.X, D.negative_half(s.X)], axis=1)
     bad = np.linalg.norm(Xf.conj().T @ Xf - np.eye(2 * n)) / np.sqrt(2 * n)
     assert bad > 1e-3
+
+
+def test_planted_mistake_dos_half_spectrum_is_caught(monkeypatch):
+    """A density summed over the positive half only (dropping Theorem 1's -lambda_j)
+    fails the normalization and symmetry pins."""
+
+    def bad_dos(lam, omega, sigma):
+        return D.gaussian_delta(omega[:, None] - lam[None, :], sigma).sum(axis=1) / (2 * lam.shape[0])
+
+    monkeypatch.setattr(D, "dos", bad_dos)
+    with pytest.raises(AssertionError):
+        test_dos_normalization_symmetry_and_peaks()

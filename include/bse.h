@@ -107,6 +107,21 @@ int bse_solve(bse_ctx* ctx, int n, const double* A, int lda, const double* B, in
               int precision, double* lambda, double* X, double* Y, bse_sol** keep,
               bse_info* info);
 
+/* Real Bethe-Salpeter problem (Section 3.2, Theorem 5, Algorithm 2): A, B real
+ * symmetric n x n (FP64, col-major, lower triangles read, host or device) with
+ * A + B > 0 and A - B > 0.
+ *   lambda  out: n positive eigenvalues, ascending
+ *   X1, X2  out (nullable): n x n real each, ld n, with
+ *           H [X1; X2] = [X1; X2] diag(lambda), H = [A B; -B -A], and
+ *           X1^T X1 - X2^T X2 = I (column signs: largest-modulus entry positive)
+ * Step 1 factors A + B and A - B separately; the SVD of L2^T L1 (step 2) is
+ * computed through the skew embedding W = [0 L1^T L2; -L2^T L1 0] by the same
+ * tridiagonal machinery as bse_solve, and X1, X2 follow as in step 3. Blocks
+ * until the outputs are written. Errors as bse_solve (BSE_ERR_NOT_DEFINITE:
+ * info->info = pivot column, counted from A + B's first column, then A - B's at n). */
+int bse_solve_real(bse_ctx* ctx, int n, const double* A, int lda, const double* B, int ldb, int precision,
+                   double* lambda, double* X1, double* X2, bse_info* info);
+
 /* Absorption weights of Eq. absp for a kept solution:
  *   w_j = (d_r^H x_j)(y_j^H d_l) / (y_j^H x_j),  j = 0..n-1
  *   d_r, d_l  2n complex128 each (host or device)

@@ -37,7 +37,8 @@ STAGE_NAMES = ["form_M", "cholesky", "form_W", "tridiag", "tdeig", "backtransfor
 
 # Every symbol the headers declare (checked by the CPU test suite).
 EXPORTS = [
-    "bse_create", "bse_destroy", "bse_set_stream", "bse_set_timing", "bse_solve", "bse_spectrum", "bse_absorption",
+    "bse_create", "bse_destroy", "bse_set_stream", "bse_set_timing", "bse_solve", "bse_solve_real", "bse_spectrum",
+    "bse_absorption",
     "bse_sol_view",
     "bse_sol_free", "bse_serve_start", "bse_submit", "bse_poll", "bse_serve_stop", "bse_solve_batched",
     "bse_last_error", "bse_version", "bse_launch_count", "bse_kprof_enable", "bse_kprof_read",
@@ -96,6 +97,7 @@ def lib() -> C.CDLL:
         "bse_set_stream": (i, [vp, vp]),
         "bse_set_timing": (i, [vp, i]),
         "bse_solve": (i, [vp, i, vp, i, vp, i, i, vp, vp, vp, C.POINTER(vp), C.POINTER(bse_info)]),
+        "bse_solve_real": (i, [vp, i, vp, i, vp, i, i, vp, vp, vp, C.POINTER(bse_info)]),
         "bse_spectrum": (i, [vp, vp, vp, vp, vp]),
         "bse_absorption": (i, [vp, vp, vp, vp, i, vp, C.c_double, vp, vp]),
         "bse_sol_view": (i, [vp, C.POINTER(i), C.POINTER(vp), C.POINTER(vp)]),
@@ -256,6 +258,28 @@ class Context:
         check(rc, "bse_solve")
         sol = Solution(solh.value) if keep else None
         return lam, X, Y, info, sol
+
+    def solve_real(self, A, B, precision="fp64", want_X=True, out=None):
+        """bse_solve_real (Algorithm 2) on real symmetric A, B (numpy host or torch
+        device, n x n FP64). Returns (lam, X1, X2, info); host inputs give numpy
+        outputs, ``out`` = dict of torch tensors (lambda, X1, X2) receives them
+        instead."""
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if isinstance(A, np.ndarray):
+            A = np.asfortranarray(A, dtype=np.float64)
+            B = np.asfortranarray(B, dtype=np.float64)
+        n = A.shape[-1]
+        if out is not None:
+            lam, X1, X2 = out.get("lambda"), out.get("X1"), out.get("X2")
+        else:
+            lam = np.empty(n, dtype=np.float64)
+            X1 = np.empty((n, n), dtype=np.float64, order="F") if want_X else None
+            X2 = np.empty((n, n), dtype=np.float64, order="F") if want_X else None
+        info = bse_info()
+        rc = lib().bse_solve_real(self.handle, n, ptr(A), n, ptr(B), n, prec, ptr(lam), ptr(X1), ptr(X2),
+                                  C.byref(info))
+        check(rc, "bse_solve_real")
+        return lam, X1, X2, info
 
     def spectrum(self, sol: Solution, d_r, d_l, out=None):
         """bse_spectrum: complex weights of Eq. absp."""

@@ -12,7 +12,7 @@ int form_M(int n, const double* A, int lda, const double* B, int ldb, double* M,
 template <typename T>
 size_t potrf_worksize(int m);
 template <typename T>
-int potrf(int m, T* A, long lda, void* work, DevStatus* st, cudaStream_t s);
+int potrf(int m, T* A, long lda, void* work, DevStatus* st, cudaStream_t s, int col_offset = 0);
 
 template <typename T>
 int form_W(int n, const T* L, long ldl, T* W, long ldw, cudaStream_t s);
@@ -31,6 +31,10 @@ int backtransform(int m, T* L, long ldl, const T* W, long ldw, const T* tau, con
                   double* X, double* Y, long ldx, void* work, cudaStream_t s);
 
 int weights(int n, const double* X, long ldx, const double* dr, const double* dl, double* w, cudaStream_t s);
+
+// real problems (k_real.cu)
+int real_to_complex(int n, const double* R, long ldr, double* Z, cudaStream_t s);
+int real_vectors(int n, const double* X, long ldx, double* X1, double* X2, long ldo, cudaStream_t s);
 
 size_t ozaki_worksize(int M, int N, int K, int s);
 // an operand of the digit-split product: K-vectors at ptr + v*ld (strided = false)

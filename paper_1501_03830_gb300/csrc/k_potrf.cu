@@ -82,7 +82,7 @@ size_t potrf_worksize(int m) {
 }
 
 template <typename T>
-int potrf(int m, T* A, long lda, void* work, DevStatus* st, cudaStream_t s) {
+int potrf(int m, T* A, long lda, void* work, DevStatus* st, cudaStream_t s, int col_offset) {
   StatusScope ss(st);
   T* Linv = reinterpret_cast<T*>(work);
   T* Ptmp = Linv + POTRF_NB * POTRF_NB;
@@ -91,7 +91,7 @@ int potrf(int m, T* A, long lda, void* work, DevStatus* st, cudaStream_t s) {
     T* Akk = A + k0 + (long)k0 * lda;
     {
       KprofScope ks(K_POTRF_DIAG, s, 0.0, kb * (double)kb * kb / 3.0 + kb * (double)kb * kb / 3.0);
-      potf2_trtri_kernel<T><<<1, 256, 0, s>>>(kb, Akk, lda, Linv, k0, st);
+      potf2_trtri_kernel<T><<<1, 256, 0, s>>>(kb, Akk, lda, Linv, k0 + col_offset, st);
     }
     BSE_LAUNCH_CHECK();
     const int r = m - k0 - kb;
@@ -111,8 +111,8 @@ int potrf(int m, T* A, long lda, void* work, DevStatus* st, cudaStream_t s) {
 
 template size_t potrf_worksize<double>(int);
 template size_t potrf_worksize<float>(int);
-template int potrf<double>(int, double*, long, void*, DevStatus*, cudaStream_t);
-template int potrf<float>(int, float*, long, void*, DevStatus*, cudaStream_t);
+template int potrf<double>(int, double*, long, void*, DevStatus*, cudaStream_t, int);
+template int potrf<float>(int, float*, long, void*, DevStatus*, cudaStream_t, int);
 
 }  // namespace bse
 
@@ -123,6 +123,6 @@ extern "C" size_t bse_stage_potrf_worksize(int m, int fp32) {
 extern "C" int bse_stage_potrf(int m, void* A, int lda, int fp32, void* work, int* dev_status, void* stream) {
   if (m < 1 || !A || lda < m || !work || !dev_status) return BSE_ERR_ARG;
   auto* st = reinterpret_cast<bse::DevStatus*>(dev_status);
-  if (fp32) return bse::potrf<float>(m, (float*)A, lda, work, st, (cudaStream_t)stream);
-  return bse::potrf<double>(m, (double*)A, lda, work, st, (cudaStream_t)stream);
+  if (fp32) return bse::potrf<float>(m, (float*)A, lda, work, st, (cudaStream_t)stream, 0);
+  return bse::potrf<double>(m, (double*)A, lda, work, st, (cudaStream_t)stream, 0);
 }

@@ -258,7 +258,7 @@ int negate_bottom(int n, double* Y, cudaStream_t s) {
 // Runs the whole pipeline on device-resident inputs into the workspace outputs
 // (ws->lam, ws->X, ws->Y). Stage events go to ev[0..8] when timing.
 int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, const double* dB, int ldb,
-                 int precision, bool want_Y, bse_info* info, cudaStream_t s) {
+                 int precision, bool want_Y, bse_info* info, cudaStream_t s, bool real_blocks) {
   const int m = 2 * n;
   cudaEvent_t* ev = c->ev;
   const bool tm = c->timing;
@@ -271,7 +271,13 @@ int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, co
   if (!f32) {
     double* W = (double*)ws->W;
     double* tau = (double*)ws->tau;
-    BSE_TRY(potrf<double>(m, ws->M, m, ws->scratch, ws->status, s));
+    if (real_blocks) {
+      // real A, B: M = diag(A + B, A - B), two Cholesky factorizations (Algorithm 2 step 1)
+      BSE_TRY(potrf<double>(n, ws->M, m, ws->scratch, ws->status, s));
+      BSE_TRY(potrf<double>(n, ws->M + n + (long)n * m, m, ws->scratch, ws->status, s, n));
+    } else {
+      BSE_TRY(potrf<double>(m, ws->M, m, ws->scratch, ws->status, s));
+    }
     if (tm) cudaEventRecord(ev[2], s);
     BSE_TRY(form_W<double>(n, ws->M, m, W, ws->ldw, s));
     if (tm) cudaEventRecord(ev[3], s);
@@ -285,7 +291,12 @@ int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, co
   } else {
     float* W = (float*)ws->W;
     float* tau = (float*)ws->tau;
-    BSE_TRY(potrf<float>(m, ws->Lf, ws->ldw, ws->scratch, ws->status, s));
+    if (real_blocks) {
+      BSE_TRY(potrf<float>(n, ws->Lf, ws->ldw, ws->scratch, ws->status, s));
+      BSE_TRY(potrf<float>(n, ws->Lf + n + (long)n * ws->ldw, ws->ldw, ws->scratch, ws->status, s, n));
+    } else {
+      BSE_TRY(potrf<float>(m, ws->Lf, ws->ldw, ws->scratch, ws->status, s));
+    }
     if (tm) cudaEventRecord(ev[2], s);
     BSE_TRY(form_W<float>(n, ws->Lf, ws->ldw, W, ws->ldw, s));
     if (tm) cudaEventRecord(ev[3], s);
@@ -398,6 +409,67 @@ extern "C" int bse_solve(bse_ctx* c, int n, const double* A, int lda, const doub
     BSE_CUDA(cudaMemcpyAsync(sol->X, ws->X, 16 * (size_t)m * n, cudaMemcpyDeviceToDevice, s));
     BSE_CUDA(cudaStreamSynchronize(s));
     *keep = sol;
+  }
+  return BSE_OK;
+}
+
+// Algorithm 2 (Section 3.2): real A = A^T, B = B^T with A + B > 0, A - B > 0.
+// Outputs lambda (n, ascending) and the real X1, X2 (n x n each, ld n) with
+// H [X1; X2] = [X1; X2] Lambda and X1^T X1 - X2^T X2 = I (Theorem 5).
+extern "C" int bse_solve_real(bse_ctx* c, int n, const double* A, int lda, const double* B, int ldb, int precision,
+                              double* lambda, double* X1, double* X2, bse_info* info) {
+  if (info) memset(info, 0, sizeof(*info));
+  if (!c || n < 1 || n > 32767 || !A || !B || lda < n || ldb < n) return BSE_ERR_ARG;
+  if (precision != BSE_FP64 && precision != BSE_MIXED && precision != BSE_MIXED_REFINED) return BSE_ERR_ARG;
+  BSE_CUDA(cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  Workspace* ws = nullptr;
+  BSE_TRY(get_workspace(c, n, precision, &ws));
+  const int m = 2 * n;
+  // the real inputs go through the X buffer (2n x n complex = 4 n^2 doubles,
+  // unused until the back-transform) and become complex A, B in the workspace
+  double* rA = ws->X;
+  double* rB = ws->X + (size_t)n * n;
+  const double* srcA = A;
+  const double* srcB = B;
+  long la = lda, lb = ldb;
+  if (!is_device_ptr(A)) {
+    BSE_CUDA(cudaMemcpy2DAsync(rA, (size_t)n * 8, A, (size_t)lda * 8, (size_t)n * 8, n, cudaMemcpyHostToDevice, s));
+    srcA = rA;
+    la = n;
+  }
+  if (!is_device_ptr(B)) {
+    BSE_CUDA(cudaMemcpy2DAsync(rB, (size_t)n * 8, B, (size_t)ldb * 8, (size_t)n * 8, n, cudaMemcpyHostToDevice, s));
+    srcB = rB;
+    lb = n;
+  }
+  BSE_TRY(real_to_complex(n, srcA, la, ws->A, s));
+  BSE_TRY(real_to_complex(n, srcB, lb, ws->B, s));
+  int rc = run_pipeline(c, ws, n, ws->A, n, ws->B, n, precision, false, info, s, true);
+  if (rc != BSE_OK) {
+    if (info) info->status = rc;
+    return rc;
+  }
+  // X1, X2 into the Y buffer (2 n^2 doubles of its 4 n^2), then out
+  double* rX1 = ws->Y;
+  double* rX2 = ws->Y + (size_t)n * n;
+  BSE_TRY(real_vectors(n, ws->X, m, (X1 && is_device_ptr(X1)) ? X1 : rX1, (X2 && is_device_ptr(X2)) ? X2 : rX2, n,
+                       s));
+  DevStatus hst;
+  BSE_CUDA(cudaMemcpyAsync(&hst, ws->status, sizeof(hst), cudaMemcpyDeviceToHost, s));
+  BSE_TRY(copy_out(lambda, ws->lam, 8 * (size_t)n, s));
+  if (X1 && !is_device_ptr(X1)) BSE_TRY(copy_out(X1, rX1, 8 * (size_t)n * n, s));
+  if (X2 && !is_device_ptr(X2)) BSE_TRY(copy_out(X2, rX2, 8 * (size_t)n * n, s));
+  BSE_CUDA(cudaStreamSynchronize(s));
+  if (info) {
+    info->precision = precision;
+    info->status = hst.code;
+    info->info = hst.info;
+  }
+  if (hst.code != 0) {
+    record_message(hst.code == BSE_ERR_NOT_DEFINITE ? "A + B or A - B is not positive definite (Cholesky pivot)"
+                                                    : "device-side failure");
+    return hst.code;
   }
   return BSE_OK;
 }

@@ -62,5 +62,5 @@ struct bse_sol {
 namespace bse {
 int get_workspace(bse_ctx* c, int n, int precision, Workspace** out);
 int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, const double* dB, int ldb,
-                 int precision, bool want_Y, bse_info* info, cudaStream_t s);
+                 int precision, bool want_Y, bse_info* info, cudaStream_t s, bool real_blocks = false);
 }  // namespace bse

@@ -11,7 +11,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle import alg1, brute
+from oracle import alg1, alg2, brute
 from oracle import definition as D
 from paper_1501_03830_gb300.synth import make_problem
 
@@ -314,6 +314,57 @@ def test_tda_eigenvalues(n, seed):
     assert _rel(s0.lam, tda) <= 1e-13
     s = D.solve(p.A, p.B)
     assert np.all(s.lam <= tda * (1 + 1e-14))
+
+
+# --- Algorithm 2 (real problems, Theorem 5) --------------------------------------
+
+
+@pytest.mark.parametrize("n,seed", [(1, 3), (6, 4), (40, 5)])
+def test_alg2_against_definition(n, seed):
+    """Algorithm 2's outputs satisfy the definitions: H [X1; X2] = [X1; X2] Lambda
+    with H = [A B; -B -A] built literally (Eq. H-real), X1^T X1 - X2^T X2 = I
+    (Theorem 5 normalization), and Lambda equals the positive eigenvalues from
+    the Hermitian-definite route of the complex oracle."""
+    p = make_problem(n, seed, real=True)
+    s = alg2.solve_real(p.A, p.B)
+    A, B = alg2.symmetrize_real(p.A, p.B)
+    H = np.block([[A, B], [-B, -A]])
+    X = np.concatenate([s.X1, s.X2], axis=0)
+    assert np.max(np.abs(H @ X - X * s.lam[None, :])) <= 1e-12 * np.abs(H).sum(axis=1).max()
+    assert np.max(np.abs(s.X1.T @ s.X1 - s.X2.T @ s.X2 - np.eye(n))) <= 1e-12
+    ref = D.solve(p.A.astype(complex), p.B.astype(complex))
+    assert _rel(s.lam, ref.lam) <= 1e-13
+
+
+def test_alg2_n1_closed_form():
+    """n = 1: lambda = sqrt((a + b)(a - b)) = sqrt(a^2 - b^2) (Section 2's real case)."""
+    a, b = 2.5, 0.7
+    s = alg2.solve_real(np.array([[a]]), np.array([[b]]))
+    assert abs(s.lam[0] - np.sqrt(a * a - b * b)) <= 1e-15 * s.lam[0]
+    assert abs(s.X1[0, 0] ** 2 - s.X2[0, 0] ** 2 - 1.0) <= 1e-14
+
+
+def test_planted_mistake_alg2_factor_is_caught(monkeypatch):
+    """Dropping the (1/2) Lambda^{-1/2} factor (the printed step 3) breaks the
+    normalization pin; swapping L1 and L2 breaks the residual pin."""
+
+    def no_factor(L1, L2, U, s, V):
+        return L2 @ U + L1 @ V, L2 @ U - L1 @ V
+
+    monkeypatch.setattr(alg2, "step3_vectors", no_factor)
+    with pytest.raises(AssertionError):
+        test_alg2_against_definition(6, 4)
+    monkeypatch.undo()
+
+    orig = alg2.step1_cholesky
+
+    def swapped(A, B):
+        L1, L2 = orig(A, B)
+        return L2, L1
+
+    monkeypatch.setattr(alg2, "step1_cholesky", swapped)
+    with pytest.raises(AssertionError):
+        test_alg2_against_definition(6, 4)
 
 
 # --- planted mistakes: each must be caught by a pin -----------------------------

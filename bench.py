@@ -549,7 +549,7 @@ def run_batched(args):
         "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": f"{len(probs)} independent BSE solves per step, n log-uniform in [32, 512] "
                                f"(sum n^3 = {sum(n ** 3 for n in ns):.3g}), {args.precision}, all in HBM",
-                   "slots": int(os.environ.get("BSE_BATCH_SLOTS", "8")),
+                   "slots": int(os.environ.get("BSE_BATCH_SLOTS", "16")),
                    "l2": "inputs + outputs of one step ~" + f"{sum(48 * n * n for n in ns) / 1e6:.0f} MB, "
                          "larger than L2"},
         "accuracy": {"checked_problems": len(pick), "max_rel_eig_err_vs_oracle": worst_eig,

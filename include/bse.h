@@ -200,7 +200,7 @@ int bse_serve_stop(bse_ctx* ctx, double timeout_s);
  * are host or device pointers (ld = ns[i]); lambdas[i] (ns[i] doubles) and
  * Xs[i] (2ns[i] x ns[i] complex128, nullable) receive the results. The
  * problems are dealt largest first to several streams of the context's GPU
- * (8 by default; BSE_BATCH_SLOTS overrides, 1..32), each with its own workspace
+ * (16 by default; BSE_BATCH_SLOTS overrides, 1..32), each with its own workspace
  * cache, so their pipelines overlap on the device; every problem runs the
  * kernels of a single bse_solve and gets bit-for-bit its results. Per-problem
  * status goes to statuses[i] (nullable); the return value is the first

@@ -233,7 +233,11 @@ static int copy_in(const double* src, int ld, int n, double* dst, cudaStream_t s
     *ldu = ld;
     return BSE_OK;
   }
-  BSE_CUDA(cudaMemcpy2DAsync(dst, (size_t)n * 16, src, (size_t)ld * 16, (size_t)n * 16, n, cudaMemcpyHostToDevice, s));
+  if (ld == n)  // contiguous: one linear copy (runs at the full pinned-memory rate)
+    BSE_CUDA(cudaMemcpyAsync(dst, src, (size_t)n * n * 16, cudaMemcpyHostToDevice, s));
+  else
+    BSE_CUDA(cudaMemcpy2DAsync(dst, (size_t)n * 16, src, (size_t)ld * 16, (size_t)n * 16, n, cudaMemcpyHostToDevice,
+                               s));
   *used = dst;
   *ldu = n;
   return BSE_OK;
@@ -433,13 +437,17 @@ extern "C" int bse_solve_real(bse_ctx* c, int n, const double* A, int lda, const
   const double* srcA = A;
   const double* srcB = B;
   long la = lda, lb = ldb;
+  auto stage = [&](double* dst, const double* src, int ld) -> cudaError_t {
+    if (ld == n) return cudaMemcpyAsync(dst, src, (size_t)n * n * 8, cudaMemcpyHostToDevice, s);
+    return cudaMemcpy2DAsync(dst, (size_t)n * 8, src, (size_t)ld * 8, (size_t)n * 8, n, cudaMemcpyHostToDevice, s);
+  };
   if (!is_device_ptr(A)) {
-    BSE_CUDA(cudaMemcpy2DAsync(rA, (size_t)n * 8, A, (size_t)lda * 8, (size_t)n * 8, n, cudaMemcpyHostToDevice, s));
+    BSE_CUDA(stage(rA, A, lda));
     srcA = rA;
     la = n;
   }
   if (!is_device_ptr(B)) {
-    BSE_CUDA(cudaMemcpy2DAsync(rB, (size_t)n * 8, B, (size_t)ldb * 8, (size_t)n * 8, n, cudaMemcpyHostToDevice, s));
+    BSE_CUDA(stage(rB, B, ldb));
     srcB = rB;
     lb = n;
   }

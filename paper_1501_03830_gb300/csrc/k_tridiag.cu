@@ -33,13 +33,12 @@ namespace bse {
 
 constexpr int TRD_NB = 64;   // panel width (the paper's n_b)
 constexpr int TRD_TB = 32;   // sub-tile edge = warp width
-constexpr int TRD_QC_MAX = 64;  // upper bound on sub-tiles per warp work item
 
 template <typename T>
 struct TrdWork {
   T* VP;        // m x 2NB: [V | P]
   T* PV;        // m x 2NB: [P | -V]
-  T* Dpart;     // direct partials   [ns][maxQ][32] (maxQ <= ns)
+  T* Dpart;     // direct partials   [ns][ns][32]: strip, piece, row
   T* Tpart;     // transposed partials [ns][ns][32]
   double* normpart;  // [kMaxGrid] per-block partial squared norms of the next column
   double* dotpart;   // [2][kMaxGrid][2NB] per-block partial V^T w, P^T w (by column parity)
@@ -206,32 +205,28 @@ __device__ __forceinline__ void warp_reduce_scatter32(T (&a)[32], int lane) {
   }
 }
 
-// Sub-tiles per SYMV work item for a trailing matrix of ns strips: about one
-// non-empty item per warp of the grid, so no warp walks a long serial chain
-// when the matrix is small.
-__device__ __forceinline__ int symv_qc(int ns, int nwarps) {
-  const long tri = (long)ns * (ns + 1) / 2;
-  int qc = (int)((tri + 4L * nwarps - 1) / (4L * nwarps));  // about four items per warp
-  return max(1, min(qc, TRD_QC_MAX));
+// SYMV work split: the T = ns (ns + 1) / 2 sub-tiles of the trailing lower
+// triangle, numbered strip by strip (strip R holds sub-tiles R (R+1)/2 ..
+// R (R+1)/2 + R, one per column block cb <= R), are cut into nw = min(warps, T)
+// contiguous non-empty ranges of equal size (+-1): warp w < nw takes
+// [floor(w T / nw), floor((w+1) T / nw)).
+// A range covers parts ("pieces") of one or a few strips; piece q of strip R is
+// the part owned by warp owner(first sub-tile of R) + q, which indexes its
+// direct partial sums.
+__device__ __forceinline__ int symv_owner(long t, int nw, long T) { return (int)(((t + 1) * nw - 1) / T); }
+
+// strip R with R (R+1) / 2 <= t < (R+1)(R+2) / 2
+__device__ __forceinline__ int symv_strip_of(long t) {
+  int R = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((long)(R + 1) * (R + 2) / 2 <= t) ++R;
+  while (R > 0 && (long)R * (R + 1) / 2 > t) --R;
+  return R;
 }
 
-// Non-empty SYMV work items of strip R: floor(R/qc) + 1. items_before(R) counts
-// the items of strips 0..R-1, so a linear item index maps back to (strip, chunk)
-// by a binary search and every warp gets real work.
-__device__ __forceinline__ long items_before(int R, int qc) {
-  const long A = R / qc, B = R % qc;
-  return (long)R + (long)qc * (A * (A - 1) / 2) + A * B;
-}
-
-__device__ __forceinline__ void item_to_strip(long i, int ns, int qc, int* R, int* q) {
-  int lo = 0, hi = ns;  // items_before(lo) <= i < items_before(hi)
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (items_before(mid, qc) <= i) lo = mid;
-    else hi = mid;
-  }
-  *R = lo;
-  *q = (int)(i - items_before(lo, qc));
+// pieces (direct partial sums) of strip R
+__device__ __forceinline__ int symv_pieces(int R, int nw, long T) {
+  const long S = (long)R * (R + 1) / 2;
+  return symv_owner(S + R, nw, T) - symv_owner(S, nw, T) + 1;
 }
 
 template <typename T>
@@ -261,7 +256,7 @@ struct Vec<double> {
 // over the CG lanes of a row group at its end. Sub-tiles on the diagonal or the
 // matrix edge take a masked scalar-load path.
 template <typename T>
-__device__ __forceinline__ void symv_item(const PanelArgs<T>& a, int j, int s, int sb, int ns, int maxQ, int Rr,
+__device__ __forceinline__ void symv_item(const PanelArgs<T>& a, int j, int s, int sb, int ns, int Rr,
                                           int cb0, int cb1, int q, T scal, int lane) {
   constexpr int VW = Vec<T>::W;   // rows per lane
   constexpr int RG = 32 / VW;     // lanes along the rows of a sub-tile
@@ -362,7 +357,7 @@ __device__ __forceinline__ void symv_item(const PanelArgs<T>& a, int j, int s, i
       yd[i] = keep + __shfl_xor_sync(0xffffffffu, send, off * RG);
     }
   }
-  a.Dpart[((long)Rr * maxQ + q) * TRD_TB + rg * VW + cg] = yd[0];
+  a.Dpart[((long)Rr * ns + q) * TRD_TB + rg * VW + cg] = yd[0];
 }
 
 // One panel of the reduction (columns j0 .. j0+nbp-1) in one cooperative launch.
@@ -438,13 +433,19 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
     {
       const int sb = s / TRD_TB;
       const int ns = ceil_div(m, TRD_TB) - sb;
-      const int qc = symv_qc(ns, nwarps);
-      const int maxQ = (ns + qc - 1) / qc;
-      const long items = items_before(ns, qc);
-      for (long item = gwarp; item < items; item += nwarps) {
-        int Rr, q;
-        item_to_strip(item, ns, qc, &Rr, &q);
-        symv_item<T>(a, j, s, sb, ns, maxQ, Rr, q * qc, min(q * qc + qc, Rr + 1), q, scal, lane);
+      const long nsub = (long)ns * (ns + 1) / 2;
+      const int nw = (int)min((long)nwarps, nsub);  // every range non-empty
+      const long t0 = (long)gwarp * nsub / nw, t1 = (long)(gwarp + 1) * nsub / nw;
+      if (gwarp < nw) {
+        int R = symv_strip_of(t0);
+        for (long t = t0; t < t1; ++R) {
+          const long S = (long)R * (R + 1) / 2;
+          const int c0 = (int)(t - S);
+          const int c1 = (int)min((long)R + 1, t1 - S);
+          const int q = gwarp - symv_owner(S, nw, nsub);
+          symv_item<T>(a, j, s, sb, ns, R, c0, c1, q, scal, lane);
+          t = S + R + 1;
+        }
       }
     }
     trace_point(a, j, 3);
@@ -455,8 +456,8 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
     {
       const int sb = s / TRD_TB;
       const int ns = ceil_div(m, TRD_TB) - sb;
-      const int qc = symv_qc(ns, nwarps);
-      const int maxQ = (ns + qc - 1) / qc;
+      const long Ttot = (long)ns * (ns + 1) / 2;
+      const int nwp = (int)min((long)nwarps, Ttot);  // the SYMV split's warp count
       const T tauj = (T)h.tau;
       const bool next = (c + 1 < a.nbp);
       // the panel's small vectors, staged once per block: V^T v, P^T v and row s of V, P
@@ -513,7 +514,7 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
         if (wid == 0) {
           const int l = s % TRD_TB;
           T y = T(0);
-          for (int q = lane; q < 1; q += 32) y += ldcg(a.Dpart + ((long)0 * maxQ + q) * TRD_TB + l);
+          for (int q = lane; q < 1; q += 32) y += ldcg(a.Dpart + ((long)0 * ns + q) * TRD_TB + l);
           {
             T py[8];
 #pragma unroll
@@ -546,7 +547,7 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
         const int r = base + (lane >> 3);
         const bool valid = r < m;
         const int Rr = r / TRD_TB - sbD, l = r % TRD_TB;
-        const int nq = valid ? Rr / qc + 1 : 0;
+        const int nq = valid ? symv_pieces(Rr, nwp, Ttot) : 0;
         const int nsv = valid ? ns : 0;
         // the row's panel entries V[r, t], P[r, t] (t = l8 + 8k < c), loaded up front
         // so their latency overlaps the partial-sum loads below
@@ -561,7 +562,7 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
         T acc[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc[k] = T(0);
-        const T* dp = a.Dpart + (long)Rr * maxQ * TRD_TB + l;
+        const T* dp = a.Dpart + (long)Rr * ns * TRD_TB + l;
         for (int q = l8; q < nq; q += 8) acc[0] += ldcg(dp + (long)q * TRD_TB);
         const T* tp = a.Tpart + (long)Rr * ns * TRD_TB + l;
         int R2 = Rr + l8;

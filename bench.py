@@ -205,6 +205,16 @@ def workload_config(args) -> dict:
 
 # --- our GPU path -----------------------------------------------------------------
 
+def algorithmic_gflops(n: int, solves_per_s: float) -> dict:
+    """Useful-work rate of a solve: Algorithm 1's stage flop counts at m = 2n --
+    Cholesky m^3/3 = 8n^3/3, W = L^T J L 4n^3/3, skew SYMV 2m^3/3 = 16n^3/3,
+    rank-2k updates 16n^3/3, back-transform 16n^3 + 8n^3 (about 38.7 n^3 in
+    total) -- times solves/s. The refinement's products are not counted."""
+    flops = (8.0 / 3 + 4.0 / 3 + 16.0 / 3 + 16.0 / 3 + 24.0) * float(n) ** 3
+    return {"value": flops * solves_per_s / 1e9, "unit": "GFLOP/s", "flops_per_solve": flops,
+            "basis": "Algorithm 1 stage counts (Cholesky, W, skew SYMV, rank-2k, back-transform); refinement not counted"}
+
+
 def aggregate_ranks(torch, dist, t_ms: float, ws: int, steps: int, device) -> tuple[float, float]:
     """Whole-job throughput of `ws` replicas that each solved `steps` problems:
     the slowest rank's time (max over ranks) and all ranks' solves / that time."""
@@ -356,6 +366,7 @@ def run_ours(args):
                 "sweeps": last.sweeps,
             },
             "fp64_path": fp64,
+            "algorithmic_gflops": algorithmic_gflops(n, value),
             "roofline": roof,
             "kernels": {k: v for k, v in kp.items() if v["launches"]},
             "cpu_baseline": cpu,

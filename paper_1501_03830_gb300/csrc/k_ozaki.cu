@@ -305,8 +305,8 @@ extern "C" size_t bse_ozaki_worksize(int M, int N, int K, int s) { return bse::o
 extern "C" int bse_ozaki_digit_bits(int K) { return K < 1 ? BSE_ERR_ARG : bse::plan(1, 1, K, 1).beta; }
 
 // C (M x N FP64, column-major, ldc) = A B with A K-major (row i at A + i*lda),
-// B column-major (column j at B + j*ldb), to about 5*s bits beyond the row/column
-// scales (beta = bse_ozaki_digit_bits(K)), on the tensor cores.
+// B column-major (column j at B + j*ldb), to about beta*s bits beyond the
+// row/column scales (beta = bse_ozaki_digit_bits(K)), on the tensor cores.
 // work: bse_ozaki_worksize(M, N, K, s) bytes.
 extern "C" int bse_ozaki_gemm(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
                               int ldc, int s, void* work, int* dev_status, void* stream) {

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY. Nothing in the product path may import, call or
 execute this package: only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use it.
 
-It shares no code with the CUDA path. Three routes are provided:
+It shares no code with the CUDA path. The modules:
 
 * :mod:`oracle.definition` -- the result Algorithm 1 must reach, written from
   the definitions (Eq. 1, Eq. GMG, Theorem 3, Eq. absp) through the
@@ -14,6 +14,8 @@ It shares no code with the CUDA path. Three routes are provided:
   intermediate results of the device pipeline stage by stage.
 * :mod:`oracle.alg2` -- Algorithm 2 (real problems, Theorem 5): two Cholesky
   factorizations, the SVD of L2^T L1, and X1, X2 from it.
+* :mod:`oracle.sbr` -- the two-stage (band, then tridiagonal) reduction of W,
+  the groundwork for a two-stage device reduction (no kernel uses it yet).
 
 :mod:`oracle.brute` adds a 50-digit mpmath eigen-decomposition of H for
 n <= 4, one of the pins that ties the oracle to something other than itself.

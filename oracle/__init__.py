@@ -16,6 +16,9 @@ It shares no code with the CUDA path. The modules:
   factorizations, the SVD of L2^T L1, and X1, X2 from it.
 * :mod:`oracle.sbr` -- the two-stage (band, then tridiagonal) reduction of W,
   the groundwork for a two-stage device reduction (no kernel uses it yet).
+* :mod:`oracle.mrrr` -- tridiagonal eigenpairs by a representation tree
+  (relatively robust L D L^T representations, child shifts for clusters,
+  twisted factorizations), the groundwork for cluster-safe device vectors.
 
 :mod:`oracle.brute` adds a 50-digit mpmath eigen-decomposition of H for
 n <= 4, one of the pins that ties the oracle to something other than itself.

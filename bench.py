@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-n", type=int, default=1280, help="oracle sample size for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-csv", default=None, help="also write the clock samples of the timed region here")
     ap.add_argument("--seed", type=int, default=8192)
     ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single",
                     help="single: one problem of size --n per step (default); batched: 512 problems, n log-uniform "
@@ -67,8 +68,9 @@ class ClockSampler:
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, csv_path: str | None = None):
         self.device = device
+        self.csv_path = csv_path  # optional copy of the raw samples
         self.proc = None
         self.lines: list[str] = []
         self.thread = None
@@ -113,9 +115,8 @@ class ClockSampler:
             for nm, val in zip(names, parts[4:8]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
-        out_dir = os.path.join(ROOT, "gpurun_out")
-        if os.path.isdir(out_dir):
-            with open(os.path.join(out_dir, "bench_clocks.csv"), "w") as f:
+        if self.csv_path:
+            with open(self.csv_path, "w") as f:
                 f.write(self.FIELDS + "\n" + "\n".join(self.lines) + "\n")
         return {
             "sm_mhz": statistics.median(sm) if sm else None,
@@ -281,7 +282,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step(args.precision)
     barrier()
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local, args.clocks_csv)
     sampler.start()
     launches0 = bse.launch_count()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -528,7 +529,7 @@ def run_batched(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(device)
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local, args.clocks_csv)
     sampler.start()
     launches0 = bse.launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -649,7 +650,7 @@ def run_serving(args):
         lat = np.array([done[i][0] - arrivals[i] for i in range(len(probs))])
         return total, lat
 
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local, args.clocks_csv)
     sampler.start()
     launches0 = bse.launch_count()
     t_burst, lat_burst = run_stream(np.zeros(len(probs)), args.precision)

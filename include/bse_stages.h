@@ -170,12 +170,6 @@ int bse_ozaki_gemm(int M, int N, int K, const double* A, int lda, const double* 
 int bse_tc32_gemm(int M, int N, int K, float alpha, const float* A, int lda, int transA, const float* B, int ldb,
                   int transB, float beta, float* C, int ldc, int uplo, int split, int* dev_status, void* stream);
 
-/* Digit products run as clusters whose CTAs share operand tiles by TMA multicast:
- * 1 (default) = 2 x 1 clusters (B shared) when the 128-row tiles pair up; 2 = 4 x 2
- * clusters (A and B shared) where the 128 x 256 tile grid divides into them, else
- * 2 x 1; 0 = one CTA per tile. Results are identical in every mode. Process-wide. */
-int bse_set_tc_pairs(int on);
-
 /* Engine of the FP32 products inside the mixed path: 1 (default) = the 3xTF32
  * tensor-core kernel above wherever the operand layout allows it, 0 = the SIMT
  * FP32 kernel everywhere (for comparisons). Process-wide. */

@@ -47,7 +47,7 @@ EXPORTS = [
     "bse_stage_backtransform_worksize", "bse_stage_backtransform", "bse_stage_weights", "bse_stage_broaden",
     "bse_stage_refine_worksize", "bse_stage_refine", "bse_tc_gemm_bf16", "bse_ozaki_worksize", "bse_ozaki_gemm",
     "bse_ozaki_digit_bits",
-    "bse_tc32_gemm", "bse_set_fp32_gemm", "bse_set_tc_pairs",
+    "bse_tc32_gemm", "bse_set_fp32_gemm",
 ]
 
 
@@ -135,7 +135,6 @@ def lib() -> C.CDLL:
         "bse_ozaki_gemm": (i, [i, i, i, vp, i, vp, i, vp, i, i, vp, vp, vp]),
         "bse_tc32_gemm": (i, [i, i, i, C.c_float, vp, i, i, vp, i, i, C.c_float, vp, i, i, i, vp, vp]),
         "bse_set_fp32_gemm": (i, [i]),
-        "bse_set_tc_pairs": (i, [i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

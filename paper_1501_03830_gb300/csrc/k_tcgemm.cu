@@ -24,7 +24,6 @@
 #include <cuda.h>
 #include <stdint.h>
 
-#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -66,39 +65,12 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
       : "memory");
 }
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
-      "%3}], [%4], %5;" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                   smem_u32(bar)),
-               "h"(mask)
-               : "memory");
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// Clusters of CM x CN CTAs (rank = i + CM j) hold the CM x CN block of output
-// tiles (tm0 + i, tn0 + j). The CTAs of one cluster column j need the same B tile
-// and those of one cluster row i the same A tile: each CTA loads 1/CM of its B
-// tile and 1/CN of its A tile and multicasts them to the CTAs that share them,
-// so a cluster reads each of its operand tiles from L2/HBM once (the co-resident
-// tiles of a large product otherwise drift apart along K and L2 stops serving
-// them: the product becomes HBM-bound). Each CTA's MMA-completion commit for a
-// stage goes to the "empty" barriers of every CTA whose loads write into it
-// (its cluster row and column, count CM + CN - 1), so no producer refills a
-// stage that a peer is still reading. CM = CN = 1 is the plain kernel.
-template <int CM, int CN>
+// One CTA per 128 x 256 output tile, tiles walked in a grouped order (a band
+// of kGroupM tile rows column by column) so the operand tiles that co-resident
+// CTAs read stay in L2.
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ TcParams P) {
-  constexpr bool MC = CM * CN > 1;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -109,34 +81,21 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t crank = 0;
-  if (MC) asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
-  const int ci = (int)crank % CM, cj = (int)crank / CM;
-  // grouped order over cluster blocks: consecutive clusters cover a band of
-  // kGroupM cluster rows, walked column by column
-  constexpr int kGroupM = 16 / CM > 0 ? 16 / CM : 1;
+  constexpr int kGroupM = 16;
   const int tiles_m = (P.M + BM - 1) / BM;
   const int tiles_n = (P.N + BN - 1) / BN;
-  const int sup_m = tiles_m / CM, sup_n = tiles_n / CN;
-  const int cl = blockIdx.x / (CM * CN);
-  const int group = cl / (kGroupM * sup_n);
+  const int group = blockIdx.x / (kGroupM * tiles_n);
   const int first_m = group * kGroupM;
-  const int gm = min(kGroupM, sup_m - first_m);
-  const int in_group = cl - group * kGroupM * sup_n;
-  const int m0 = ((first_m + in_group % gm) * CM + ci) * BM;
-  const int n0 = ((in_group / gm) * CN + cj) * BN;
-  // multicast masks: the CTAs sharing this CTA's A tile (same i) and B tile (same j)
-  uint16_t row_mask = 0, col_mask = 0;
-#pragma unroll
-  for (int t = 0; t < CN; ++t) row_mask |= (uint16_t)(1u << (ci + CM * t));
-#pragma unroll
-  for (int t = 0; t < CM; ++t) col_mask |= (uint16_t)(1u << (t + CM * cj));
+  const int gm = min(kGroupM, tiles_m - first_m);
+  const int in_group = blockIdx.x - group * kGroupM * tiles_n;
+  const int m0 = (first_m + in_group % gm) * BM;
+  const int n0 = (in_group / gm) * BN;
   const int KB = (P.K + BK - 1) / BK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], MC ? CM + CN - 1 : 1);
+      mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -149,8 +108,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
   tc_fence_before();
   __syncthreads();
-  // peers may signal this CTA's barriers only after they are initialised
-  if (MC) cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
@@ -184,15 +141,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int yb = P.b_digit[p_u] * P.b_rows + n0;
         uint8_t* sa = smem + st * STAGE_BYTES;
         mbar_expect_tx(&full[st], STAGE_BYTES);
-        if (CN > 1)
-          tma_load_2d_mc(sa + cj * (A_BYTES / CN), &tmA, p_kb * BK, ya + cj * (BM / CN), &full[st], row_mask);
-        else
-          tma_load_2d(sa, &tmA, p_kb * BK, ya, &full[st]);
-        if (CM > 1)
-          tma_load_2d_mc(sa + A_BYTES + ci * (B_BYTES / CM), &tmB, p_kb * BK, yb + ci * (BN / CM), &full[st],
-                         col_mask);
-        else
-          tma_load_2d(sa + A_BYTES, &tmB, p_kb * BK, yb, &full[st]);
+        tma_load_2d(sa, &tmA, p_kb * BK, ya, &full[st]);
+        tma_load_2d(sa + A_BYTES, &tmB, p_kb * BK, yb, &full[st]);
         issued |= 1u << st;
         last_par = (last_par & ~(1u << st)) | (ph << st);
         ++p_it;
@@ -222,10 +172,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk)
           umma_bf16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, (kc | kk) != 0);
-        if (MC)
-          umma_commit_mc(&empty[st], (uint16_t)(row_mask | col_mask));
-        else
-          umma_commit(&empty[st]);
+        umma_commit(&empty[st]);
         ++m_it;
         ++m_kb;
         if (kc == P.chunk_kb - 1 || m_kb == KB) {
@@ -324,8 +271,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     tmem_dealloc(tmem_base, TMEM_COLS);
   }
   if (threadIdx.x == 0 && *err && P.status) atomicCAS(P.status, 0, *err);
-  // no CTA leaves while a peer may still write its shared memory
-  if (MC) cluster_sync_all();
 }
 
 // ---- host side -------------------------------------------------------------
@@ -376,9 +321,6 @@ static int make_map(CUtensorMap* map, const void* base, long rows, long K, long 
   return make_tensor_map_2d(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, K, rows, ldk * 2, BK, box_rows);
 }
 
-static std::atomic<int> g_pair{1};
-static int pair_mode() { return g_pair.load(std::memory_order_relaxed); }
-
 int tc_gemm(const TcProblem& pb, cudaStream_t s) {
   if (pb.M <= 0 || pb.N <= 0 || pb.K <= 0 || pb.units <= 0) return BSE_OK;
   if (pb.units > kMaxUnits || pb.chunk_kb < 1 || !pb.fold[pb.units - 1] || (pb.ldk % 8) != 0 ||
@@ -390,28 +332,15 @@ int tc_gemm(const TcProblem& pb, cudaStream_t s) {
   static std::once_flag attr_once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (attr_err == cudaSuccess)
-      attr_err = cudaFuncSetAttribute(tc_gemm_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (attr_err == cudaSuccess)
-      attr_err = cudaFuncSetAttribute(tc_gemm_kernel<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   });
   if (attr_err != cudaSuccess) {
     record_error("cudaFuncSetAttribute(tc_gemm_kernel)", attr_err, __FILE__, __LINE__);
     return BSE_ERR_CUDA;
   }
-  // cluster shape: 4 x 2 when the tile grid divides into it, else 2 x 1, else none
-  const int tiles_m = (pb.M + BM - 1) / BM, tiles_n = (pb.N + BN - 1) / BN;
-  int cm = 1, cn = 1;
-  if (pair_mode() >= 2 && tiles_m % 4 == 0 && tiles_n % 2 == 0) {
-    cm = 4;
-    cn = 2;
-  } else if (pair_mode() >= 1 && tiles_m % 2 == 0) {
-    cm = 2;
-  }
   CUtensorMap ma, mb;
-  BSE_TRY(make_map(&ma, pb.A, (long)pb.a_rows * pb.a_digits, pb.K, pb.ldk, BM / cn));
-  BSE_TRY(make_map(&mb, pb.B, (long)pb.b_rows * pb.b_digits, pb.K, pb.ldk, BN / cm));
+  BSE_TRY(make_map(&ma, pb.A, (long)pb.a_rows * pb.a_digits, pb.K, pb.ldk, BM));
+  BSE_TRY(make_map(&mb, pb.B, (long)pb.b_rows * pb.b_digits, pb.K, pb.ldk, BN));
   TcParams P{};
   P.M = pb.M; P.N = pb.N; P.K = pb.K;
   P.a_rows = pb.a_rows; P.b_rows = pb.b_rows;
@@ -426,27 +355,8 @@ int tc_gemm(const TcProblem& pb, cudaStream_t s) {
   P.status = pb.status;
   const long tiles = (long)((pb.M + BM - 1) / BM) * ((pb.N + BN - 1) / BN);
   KprofScope ks(K_GEMM_TC, s, 0.0, 2.0 * pb.M * (double)pb.N * pb.K * pb.units);
-  if (cm * cn == 1) {
-    tc_gemm_kernel<1, 1><<<(unsigned)tiles, THREADS, SMEM_BYTES, s>>>(ma, mb, P);
-    BSE_LAUNCH_CHECK();
-    return BSE_OK;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)tiles);
-  cfg.blockDim = dim3(THREADS);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cm * cn;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (cm == 4)
-    BSE_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<4, 2>, ma, mb, P));
-  else
-    BSE_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<2, 1>, ma, mb, P));
+  tc_gemm_kernel<<<(unsigned)tiles, THREADS, SMEM_BYTES, s>>>(ma, mb, P);
+  BSE_LAUNCH_CHECK();
   return BSE_OK;
 }
 
@@ -467,13 +377,3 @@ extern "C" int bse_tc_gemm_bf16(int M, int N, int K, const void* A, const void* 
   return bse::tc::tc_gemm(pb, (cudaStream_t)stream);
 }
 
-// 1 (default): digit products whose row tiles pair up run as 2-CTA clusters
-// sharing B tiles by TMA multicast; 2: 4 x 2 clusters sharing A and B tiles where
-// the tile grid allows (measured slower on GB300: 8-CTA clusters leave SMs of a
-// GPC idle and tie every stage to the slowest of five producers); 0: one CTA per
-// tile everywhere.
-extern "C" int bse_set_tc_pairs(int on) {
-  if (on < 0 || on > 2) return BSE_ERR_ARG;
-  bse::tc::g_pair.store(on);
-  return BSE_OK;
-}

@@ -42,8 +42,6 @@ def run(argv=None) -> dict:
     ap.add_argument("--split", type=int, default=1, help="tc32: 1 = 3xTF32, 0 = one TF32 pass")
     ap.add_argument("--m", type=int, default=8192, help="matrix order (tridiag, tdeig)")
     ap.add_argument("--fp64", action="store_true", help="tridiag in FP64 instead of FP32")
-    ap.add_argument("--pairs", type=int, default=1,
-                    help="ozaki: 4x2 multicast clusters (2), 2x1 (1) or one CTA per tile (0)")
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
     L = bse.lib()
@@ -60,7 +58,6 @@ def run(argv=None) -> dict:
         ms = _timed(torch, fn, a.reps)
         out.update(M=a.M, N=a.N, K=a.K, split=a.split, ms=ms, tflops=2.0 * a.M * a.N * a.K / ms / 1e9)
     elif a.stage == "ozaki":
-        bse.check(L.bse_set_tc_pairs(a.pairs), "pairs")
         A = torch.randn(a.M, a.K, dtype=torch.float64, device="cuda", generator=g)
         B = torch.randn(a.N, a.K, dtype=torch.float64, device="cuda", generator=g)
         C = torch.zeros(a.N, a.M, dtype=torch.float64, device="cuda")
@@ -69,7 +66,7 @@ def run(argv=None) -> dict:
                                                 a.s, work.data_ptr(), st.data_ptr(), None), "ozaki")
         ms = _timed(torch, fn, a.reps)
         units = a.s * (a.s + 1) // 2
-        out.update(M=a.M, N=a.N, K=a.K, s=a.s, units=units, pairs=a.pairs, ms=ms,
+        out.update(M=a.M, N=a.N, K=a.K, s=a.s, units=units, ms=ms,
                    fp64_tflops=2.0 * a.M * a.N * a.K / ms / 1e9,
                    bf16_tflops=2.0 * a.M * a.N * a.K * units / ms / 1e9)
     elif a.stage == "tridiag":

@@ -179,9 +179,11 @@ typedef struct bse_result {
   double refine_dlam;
 } bse_result;
 
-/* Start the request loop (a scheduler thread and `slots` streams). Requests
- * are admitted while their workspace fits the HBM budget; small problems are
- * packed into batched launches. */
+/* Start the request loop: `slots` worker threads, each with its own stream and
+ * workspace. A queued request is admitted (first fit in arrival order) when a
+ * slot is free and its workspace fits the HBM budget next to the running ones;
+ * each admitted request runs the kernels of one bse_solve on its slot's stream,
+ * so requests on different slots overlap on the device. */
 int bse_serve_start(bse_ctx* ctx, int slots);
 
 /* Queue a request; never blocks. BSE_ERR_BUSY if the queue is full. */

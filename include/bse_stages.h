@@ -66,6 +66,17 @@ int bse_stage_tridiag(int m, void* W, int ldw, double* e, void* tau, int fp32, v
  * (layout [column][5][block], unsigned 64-bit); NULL turns it off. The buffer must
  * hold columns * 5 * bse_stage_tridiag_grid(m, fp32) entries. */
 int bse_debug_trace_tridiag(void* dev_buffer, int columns);
+
+/* Test hook for failure detection without a GPU fault: the number of polls after
+ * which a grid-barrier wait of the tridiagonal panel kernel gives up (polls > 0),
+ * or 0 to restore the default (2^25 polls, about 2 s). With a tiny value the
+ * blocks of the next panel launch stop waiting for one another: each records
+ * BSE_ERR_TIMEOUT in the device status word and returns, the stage returns
+ * normally, and the status reaches the host through dev_status / bse_info. The
+ * barrier words are reset at the start of every reduction, so the next solve on
+ * the same context runs normally once the default is restored. Process-wide;
+ * not for concurrent use. */
+int bse_debug_barrier_spin(long polls);
 /* Blocks in the cooperative grid of the panel kernel (the largest launched). */
 int bse_stage_tridiag_grid(int m, int fp32);
 

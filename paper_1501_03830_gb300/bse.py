@@ -43,7 +43,7 @@ EXPORTS = [
     "bse_sol_free", "bse_serve_start", "bse_submit", "bse_poll", "bse_serve_stop", "bse_solve_batched",
     "bse_last_error", "bse_version", "bse_launch_count", "bse_kprof_enable", "bse_kprof_read",
     "bse_stage_form_M", "bse_stage_potrf_worksize", "bse_stage_potrf", "bse_stage_form_W",
-    "bse_stage_tridiag_worksize", "bse_stage_tridiag", "bse_debug_trace_tridiag", "bse_stage_tridiag_grid", "bse_stage_tdeig_worksize", "bse_stage_tdeig", "bse_stage_tdeig_noalloc",
+    "bse_stage_tridiag_worksize", "bse_stage_tridiag", "bse_debug_trace_tridiag", "bse_debug_barrier_spin", "bse_stage_tridiag_grid", "bse_stage_tdeig_worksize", "bse_stage_tdeig", "bse_stage_tdeig_noalloc",
     "bse_stage_backtransform_worksize", "bse_stage_backtransform", "bse_stage_weights", "bse_stage_broaden",
     "bse_stage_refine_worksize", "bse_stage_refine", "bse_tc_gemm_bf16", "bse_ozaki_worksize", "bse_ozaki_gemm",
     "bse_ozaki_digit_bits",
@@ -119,6 +119,7 @@ def lib() -> C.CDLL:
         "bse_stage_tridiag_worksize": (sz, [i, i]),
         "bse_stage_tridiag": (i, [i, vp, i, vp, vp, i, vp, vp, vp]),
         "bse_debug_trace_tridiag": (i, [vp, i]),
+        "bse_debug_barrier_spin": (i, [C.c_long]),
         "bse_stage_tridiag_grid": (i, [i, i]),
         "bse_stage_tdeig_worksize": (sz, [i]),
         "bse_stage_tdeig": (i, [i, vp, vp, vp, vp, vp, vp]),

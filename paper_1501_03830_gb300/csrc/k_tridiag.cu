@@ -121,6 +121,7 @@ struct PanelArgs {
   int vec;  // 16-byte vector loads of W are aligned (ldw multiple of 16 B / sizeof(T), W 16-B aligned)
   unsigned long long* trace;  // optional: [column][5 points][block] globaltimer stamps
   int trace_cols;
+  long spin;  // polls before a grid-barrier wait gives up
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -135,11 +136,11 @@ __device__ __forceinline__ void trace_point(const PanelArgs<T>& a, int col, int 
     a.trace[((long)col * 5 + point) * gridDim.x + blockIdx.x] = gtimer();
 }
 
-// Grid-wide barrier for a cooperative launch. The wait is bounded: after ~2 s
-// it records BSE_ERR_TIMEOUT and every block returns at its next barrier. A
-// failure recorded by any block (or an earlier stage) also makes all blocks
-// return.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, DevStatus* st) {
+// Grid-wide barrier for a cooperative launch. The wait is bounded: after
+// `spin` polls (2^25, about 2 s, unless a test lowers it) it records
+// BSE_ERR_TIMEOUT and every block returns at its next barrier. A failure
+// recorded by any block (or an earlier stage) also makes all blocks return.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, DevStatus* st, long spin) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -155,7 +156,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, DevStatus* st) {
     } else {
       long it = 0;
       while (*vgen == g) {
-        if (++it > (1L << 25)) {
+        if (++it > spin) {
           set_status(st, BSE_ERR_TIMEOUT, 1);
           ok = 0;
           break;
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
     const int j = a.j0 + c;
     const int s = j + 1;
     trace_point(a, j, 0);
-    if (!grid_barrier(a.bar, a.st)) return;
+    if (!grid_barrier(a.bar, a.st, a.spin)) return;
     trace_point(a, j, 1);
 
     // ---------------- phase B/C ----------------
@@ -449,7 +450,7 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
       }
     }
     trace_point(a, j, 3);
-    if (!grid_barrier(a.bar, a.st)) return;
+    if (!grid_barrier(a.bar, a.st, a.spin)) return;
     trace_point(a, j, 4);
 
     // ---------------- phase D (+ A of the next column) ----------------
@@ -817,6 +818,8 @@ __global__ void __launch_bounds__(512) trd_small_kernel(int m, T* __restrict__ W
 
 static unsigned long long* g_trace = nullptr;
 static int g_trace_cols = 0;
+constexpr long kBarrierSpin = 1L << 25;
+static long g_barrier_spin = kBarrierSpin;
 
 template <typename T>
 int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStream_t st, DevStatus* status) {
@@ -873,6 +876,7 @@ int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStr
     pa.vec = ((ldw * (long)sizeof(T)) % 16 == 0) && ((reinterpret_cast<uintptr_t>(W) % 16) == 0);
     pa.trace = g_trace;
     pa.trace_cols = g_trace_cols;
+    pa.spin = g_barrier_spin;
     if (grid * 256 < rows + 1 && grid < nsm * per_sm) {
       record_message("tridiagonal panel grid too small");
       return BSE_ERR_CUDA;
@@ -910,6 +914,12 @@ template int tridiagonalize<float>(int, float*, long, double*, float*, void*, cu
 extern "C" int bse_debug_trace_tridiag(void* dev_buffer, int columns) {
   bse::g_trace = reinterpret_cast<unsigned long long*>(dev_buffer);
   bse::g_trace_cols = dev_buffer ? columns : 0;
+  return BSE_OK;
+}
+
+extern "C" int bse_debug_barrier_spin(long polls) {
+  if (polls < 0) return BSE_ERR_ARG;
+  bse::g_barrier_spin = polls == 0 ? bse::kBarrierSpin : polls;
   return BSE_OK;
 }
 

@@ -7,7 +7,8 @@ can compute one by one:
     lambda_k (1 + 1e-10), which pins lambda_k to 1e-10 relative (n = 2048);
   * scaled residuals ||H x_j - lambda_j x_j|| / (||H||_F ||x_j||) of sampled
     columns against the bar 100 n eps, and biorthogonality y_i^H x_j = delta_ij
-    of sampled pairs (Theorem 3), at both sizes;
+    of sampled pairs and of a contiguous block around the closest pair of
+    eigenvalues (Theorem 3), at both sizes;
   * the real case (Eq. H-real) at n = 2048: every lambda^2 against the
     eigenvalues of (A - B)(A + B), computed through the Cholesky factor of A + B
     as a symmetric eigenproblem.
@@ -57,6 +58,25 @@ def _biorth(x, n):
     return np.max(np.abs(y.conj().T @ x - np.eye(x.shape[1])))
 
 
+def _block_biorth(x, n):
+    """max |Y_f^H X_f - I| over a block of columns and their negative-half partners
+    (Theorem 3: x_- = [conj(x2); conj(x1)], y = S x on the positive half and
+    y = -S x on the negative half) -- the block's part of Table 1's metric."""
+    xn = np.concatenate([x[n:].conj(), x[:n].conj()], axis=0)
+    Xf = np.concatenate([x, xn], axis=1)
+    s = np.concatenate([np.ones(n), -np.ones(n)])[:, None]
+    Yf = np.concatenate([s * x, -s * xn], axis=1)
+    return np.max(np.abs(Yf.conj().T @ Xf - np.eye(Xf.shape[1])))
+
+
+def _closest_block(lam, width=64):
+    """Contiguous columns around the smallest relative gap of the spectrum."""
+    g = np.diff(lam) / lam[1:]
+    k = int(np.argmin(g))
+    a = max(0, min(k - width // 2 + 1, lam.shape[0] - width))
+    return np.arange(a, a + width), float(g[k])
+
+
 def _sample(n, k=48):
     return np.unique(np.concatenate([[0, 1, n // 2, n - 2, n - 1], np.linspace(0, n - 1, k).astype(int)]))
 
@@ -94,6 +114,8 @@ def test_mixed_refined_n2048_matches_fp64():
     x = _columns(torch, X, n, cols)
     assert np.max(D.scaled_residuals(p.A, p.B, lam[cols], x)) <= 100 * n * EPS
     assert _biorth(x, n) <= 1e-10
+    blk, gmin = _closest_block(lam)
+    assert _block_biorth(_columns(torch, X, n, blk), n) <= 1e-12, gmin
 
 
 def test_real_case_n2048_all_eigenvalues():
@@ -112,10 +134,13 @@ def test_real_case_n2048_all_eigenvalues():
 
 def test_mixed_refined_n8192_bench_configuration():
     """The benchmark's workload (n = 8192, seed 8192, mixed + FP64 refinement):
-    sampled residuals against 100 n eps, sampled biorthogonality, ascending
-    positive spectrum, and agreement of the refined eigenvalues with the
-    residual-based first-order bound |d lambda_j| <= ||r_j|| ||y_j|| / |y_j^H x_j|
-    (y_j^H x_j = 1), evaluated on the sampled columns."""
+    * eigenvalue positions to 1e-10 by Sylvester inertia (Schur-complement count)
+      at the smallest and largest eigenvalue and at the one with the smallest
+      relative gap to its neighbour;
+    * biorthogonality (Theorem 3, Table 1's metric restricted to a block) over 64
+      contiguous columns around the smallest relative gap, and their negative-half
+      partners, to 1e-12;
+    * sampled scaled residuals against 100 n eps and an ascending positive spectrum."""
     torch = torch_cuda()
     p = make_problem(8192, 8192)
     n = p.n
@@ -124,13 +149,14 @@ def test_mixed_refined_n8192_bench_configuration():
     assert info.status == 0 and info.sweeps >= 1
     assert info.refine_resid <= 100 * n * EPS
     assert np.all(np.diff(lam) >= 0) and lam[0] > 0
+    blk, gmin = _closest_block(lam)
+    xb = _columns(torch, X, n, blk)
+    assert _block_biorth(xb, n) <= 1e-12, (_block_biorth(xb, n), gmin)
     cols = _sample(n, 24)
     x = _columns(torch, X, n, cols)
     r = D.scaled_residuals(p.A, p.B, lam[cols], x)
     assert np.max(r) <= 100 * n * EPS, np.max(r)
-    assert _biorth(x, n) <= 1e-10
-    # first-order eigenvalue error bound from the sampled residuals
-    normH = np.sqrt(2.0 * (np.linalg.norm(p.A) ** 2 + np.linalg.norm(p.B) ** 2))
-    xn = np.linalg.norm(x, axis=0)
-    bound = r * normH * xn * xn / lam[cols]
-    assert np.max(bound) <= 1e-9, np.max(bound)
+    kg = int(blk[0] + np.argmin(np.diff(lam[blk]) / lam[blk][1:]))
+    for k in (0, kg, n - 1):
+        assert D.eig_count_below_schur(p.A, p.B, lam[k] * (1 - 1e-10)) == k
+        assert D.eig_count_below_schur(p.A, p.B, lam[k] * (1 + 1e-10)) == k + 1

@@ -1,7 +1,7 @@
 """Spectral density (Eq. DOS) and broadened absorption spectrum (Eq. absp) on the
 GPU, against the oracle's plain sums, and the Tamm-Dancoff comparison of
 Section 5 (B = 0 gives the eigenvalues of A; with B the BSE eigenvalues lie
-below them, Theorem TDA)."""
+below them, Theorem 4)."""
 import numpy as np
 import pytest
 

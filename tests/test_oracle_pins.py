@@ -22,6 +22,38 @@ def _rel(a, b):
     return np.max(np.abs(a - b) / np.abs(b))
 
 
+@pytest.mark.parametrize("n,seed", [(1, 5), (37, 6), (300, 7)])
+def test_eig_count_below_schur(n, seed):
+    """Sylvester inertia through the Schur complement of S - Omega/sigma (Eq. cond):
+    exactly k eigenvalues below lambda_k (1 - 1e-10) and k + 1 below lambda_k (1 + 1e-10),
+    the same counts as the full indefinite factorization."""
+    p = make_problem(n, seed)
+    s = D.solve(p.A, p.B)
+    for k in sorted({0, n // 3, n - 1}):
+        for f, want in ((1 - 1e-10, k), (1 + 1e-10, k + 1)):
+            sig = s.lam[k] * f
+            assert D.eig_count_below_schur(p.A, p.B, sig) == want
+            assert D.eig_count_below(p.A, p.B, sig) == want
+
+
+def test_planted_mistake_schur_sign_is_caught(monkeypatch):
+    """Subtracting the Schur term instead of adding it (K12 K22^{-1} K21 has two minus
+    signs) miscounts and fails the inertia pin."""
+    import scipy.linalg as sla
+
+    def bad(A, B, sigma):
+        A, B = D.symmetrize_lower(A, B)
+        n = A.shape[0]
+        Lg = np.linalg.cholesky(np.eye(n) + A.conj() / sigma)
+        Z = sla.solve_triangular(Lg, B.conj() / sigma, lower=True)
+        Sc = np.eye(n) - A / sigma - Z.conj().T @ Z
+        return int(np.sum(np.linalg.eigvalsh((Sc + Sc.conj().T) / 2) > 0))
+
+    monkeypatch.setattr(D, "eig_count_below_schur", bad)
+    with pytest.raises(AssertionError):
+        test_eig_count_below_schur(37, 6)
+
+
 # --- closed forms -------------------------------------------------------------
 
 
@@ -109,7 +141,7 @@ def test_pairing(n, seed):
 
 @pytest.mark.parametrize("n,seed", [(8, 2), (64, 0), (150, 4)])
 def test_tda_upper_bound(n, seed):
-    """Theorem 5: lambda_j(H) <= lambda_j(A) for every j (both sorted the same way)."""
+    """Theorem 4: lambda_j(H) <= lambda_j(A) for every j (both sorted the same way)."""
     p = make_problem(n, seed)
     s = D.solve(p.A, p.B)
     A, _ = D.symmetrize_lower(p.A, p.B)
@@ -120,7 +152,7 @@ def test_tda_upper_bound(n, seed):
 @pytest.mark.parametrize("n,seed", [(5, 1), (64, 3)])
 def test_real_case_product_eigenproblem(n, seed):
     """Real case (Eq. H-real): lambda^2 are the eigenvalues of (A-B)(A+B), computed here as
-    eig(L1^T (A-B) L1) with A+B = L1 L1^T (Section 2.1 and Theorem 4)."""
+    eig(L1^T (A-B) L1) with A+B = L1 L1^T (Section 2.1)."""
     p = make_problem(n, seed, real=True)
     s = D.solve(p.A.astype(complex), p.B.astype(complex))
     A = np.tril(p.A) + np.tril(p.A, -1).T
@@ -203,7 +235,7 @@ def test_theorem2_embedding():
     M = D.build_M(A, B)
     assert np.max(np.abs(lhs - (-1j) * D.build_J(n) @ M)) <= 1e-14
     assert np.max(np.abs(M - M.T)) == 0.0
-    # and the Theorem 5 proof: Q^H Omega Q = Atilde + Btilde, i.e. M (it is positive definite)
+    # and the Theorem 4 proof: Q^H Omega Q = Atilde + Btilde, i.e. M (it is positive definite)
     assert np.max(np.abs(Q.conj().T @ D.build_Omega(A, B) @ Q - M)) <= 1e-14
 
 
@@ -307,7 +339,7 @@ def test_absorption_sum_rule(n, seed):
 def test_tda_eigenvalues(n, seed):
     """B = 0 makes H block diagonal (Eq. 1): its positive eigenvalues are those of
     A exactly, the Tamm-Dancoff values; with B != 0 every lambda_j(H) lies below
-    lambda_j(A) (Theorem TDA)."""
+    lambda_j(A) (Theorem 4)."""
     p = make_problem(n, seed)
     tda = D.tda_eigenvalues(p.A)
     s0 = D.solve(p.A, np.zeros_like(p.B))

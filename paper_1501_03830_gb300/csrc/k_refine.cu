@@ -515,6 +515,17 @@ __global__ void __launch_bounds__(256) ref_cluster_rr(int n, const int2* __restr
   }
 }
 
+// Cluster threshold of the final Rayleigh-Ritz polish (relative gap): 20x the
+// first sweep's eigenvalue change, within [floor, cap].
+#ifndef BSE_FINAL_TAU_FLOOR
+#define BSE_FINAL_TAU_FLOOR 0.0
+#endif
+#ifndef BSE_FINAL_TAU_CAP
+#define BSE_FINAL_TAU_CAP 1e-3
+#endif
+constexpr double kFinalTauFloor = BSE_FINAL_TAU_FLOOR;
+constexpr double kFinalTauCap = BSE_FINAL_TAU_CAP;
+
 // Runs of consecutive eigenvalues with relative gaps below tau, split to at most
 // kRRMax at their widest internal gap; cluster_id[j] = first index of j's run.
 static void find_clusters(const std::vector<double>& lam, double tau, std::vector<int2>& out, std::vector<int>& id) {
@@ -616,7 +627,7 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
       // and every column is rescaled to y^H x = 1 exactly.
       BSE_CUDA(cudaMemcpyAsync(hlam.data(), lam, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
       BSE_CUDA(cudaStreamSynchronize(s));
-      find_clusters(hlam, fmin(1e-3, fmax(1e-13, 20.0 * dl_level)), clusters, cid);
+      find_clusters(hlam, fmin(kFinalTauCap, fmax(kFinalTauFloor, fmax(1e-13, 20.0 * dl_level))), clusters, cid);
       if (!clusters.empty()) {
         BSE_CUDA(cudaMemcpyAsync(w.clus, clusters.data(), sizeof(int2) * clusters.size(), cudaMemcpyHostToDevice, s));
         kcount(1);

@@ -39,6 +39,9 @@ namespace bse {
 
 static inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+constexpr int kBandW = 48;      // band biorthogonalization: index distance 1..kBandW
+constexpr int kBandChunk = 16;  // couplings per thread block pass
+
 struct RefWork {
   double *Ur, *Ui, *Pr, *Pi;          // FP64 U = Q^H X and P = M U (then R)
   float *Urf, *Uif, *Rrf, *Rif;       // FP32 copies for the projections
@@ -51,6 +54,7 @@ struct RefWork {
   void* oz;                   // digit-split tensor-core product workspace (M U)
   void* oz2;                  // same for the projections and the update
   double* Gbig;               // 2n x 2n: [Ur Ui]^T [Rr Ri]
+  double2* Bband;             // n x kBandW couplings of the band biorthogonalization
 };
 
 // digits of the correction-sized products: ~25 bits
@@ -62,7 +66,8 @@ static bool refine_uses_tc(int n) { return 2 * n >= 1024; }
 size_t refine_worksize(int n) {
   const size_t m = 2 * (size_t)n;
   size_t b = 2 * al256(16 * m * n) + 6 * al256(4 * m * n) + 8 * al256(4 * (size_t)n * n) + 2 * al256(8 * (size_t)n) +
-             al256(64) + al256(64) + al256(4 * (size_t)n) + al256(8 * ((size_t)n / 2 + 2));
+             al256(64) + al256(64) + al256(4 * (size_t)n) + al256(8 * ((size_t)n / 2 + 2)) +
+             al256(16 * (size_t)n * kBandW);
   if (refine_uses_tc(n)) {
     b += al256(ozaki_worksize((int)m, 2 * n, (int)m, ozaki_digits((int)m)));
     b += al256(ozaki_worksize(2 * n, 2 * n, (int)m, corr_digits(m)));
@@ -96,6 +101,7 @@ static RefWork carve_ref(void* work, int n) {
   w.maxes = (unsigned long long*)take(64);
   w.cid = (int*)take(4 * (size_t)n);
   w.clus = (int2*)take(8 * ((size_t)n / 2 + 2));
+  w.Bband = (double2*)take(16 * (size_t)n * kBandW);
   w.oz = w.oz2 = nullptr;
   w.Gbig = nullptr;
   if (refine_uses_tc(n)) {
@@ -560,6 +566,113 @@ static void find_clusters(const std::vector<double>& lam, double tau, std::vecto
   }
 }
 
+// ---- band biorthogonalization (end of the refinement) ------------------------
+// After the sweeps the basis is biorthogonal to first order only: pairs of
+// nearby eigenvalues keep a coupling b_ij = u_i^H K u_j (= y_i^H x_j, Theorem 3)
+// of up to ~1e-9, which falls off with the index distance |i - j| (measured at
+// n = 8192: ~1e-11 at distance 10, below 1e-12 beyond ~40). A symmetric
+// (Loewdin) step U <- U (I - E/2), E = U^H K U - I restricted to the band
+// 0 < |i - j| <= kBandW, removes it to second order without dividing by any gap;
+// the diagonal of E is handled by the exact rescaling that follows. b_ij needs
+// FP64 accumulation (it is a cancelling sum of O(1) terms); the update is as
+// small as b_ij, so FP32 carries it.
+
+// Bband[j * kBandW + q] = u_i^H K u_j for i = j - 1 - q (grid: n x kBandW / kBandChunk)
+__global__ void __launch_bounds__(256) ref_band_gram(int n, const double* __restrict__ Ur,
+                                                     const double* __restrict__ Ui, double2* __restrict__ Bband) {
+  __shared__ double red[8][2 * kBandChunk];
+  const int j = blockIdx.x, q0 = blockIdx.y * kBandChunk;
+  const long m = 2L * n, cj = (long)j * m;
+  const int nq = max(0, min(kBandChunk, j - q0));  // i = j-1-q >= 0
+  double ar[kBandChunk], ai[kBandChunk];
+#pragma unroll
+  for (int q = 0; q < kBandChunk; ++q) ar[q] = ai[q] = 0.0;
+  if (nq > 0) {
+    for (int k = threadIdx.x; k < n; k += 256) {
+      // K u_j: top = -i u_bot = (ub.y, -ub.x), bottom = i u_top = (-ut.y, ut.x)
+      const double tr = Ur[k + cj], ti = Ui[k + cj], br = Ur[n + k + cj], bi = Ui[n + k + cj];
+      const double ktr = bi, kti = -br, kbr = -ti, kbi = tr;
+#pragma unroll
+      for (int q = 0; q < kBandChunk; ++q) {
+        if (q < nq) {
+          const long ci = (long)(j - 1 - q0 - q) * m;
+          const double xr = Ur[k + ci], xi = Ui[k + ci], yr = Ur[n + k + ci], yi = Ui[n + k + ci];
+          // conj(x) * kt + conj(y) * kb
+          ar[q] = fma(xr, ktr, fma(xi, kti, fma(yr, kbr, fma(yi, kbi, ar[q]))));
+          ai[q] = fma(xr, kti, fma(-xi, ktr, fma(yr, kbi, fma(-yi, kbr, ai[q]))));
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kBandChunk; ++q) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      ar[q] += __shfl_xor_sync(0xffffffffu, ar[q], o);
+      ai[q] += __shfl_xor_sync(0xffffffffu, ai[q], o);
+    }
+  }
+  const int wid = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int q = 0; q < kBandChunk; ++q) {
+      red[wid][2 * q] = ar[q];
+      red[wid][2 * q + 1] = ai[q];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kBandChunk) {
+    const int q = threadIdx.x;
+    double sr = 0.0, si = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      sr += red[w][2 * q];
+      si += red[w][2 * q + 1];
+    }
+    Bband[(long)j * kBandW + q0 + q] = (q < nq) ? make_double2(sr, si) : make_double2(0.0, 0.0);
+  }
+}
+
+// dU_j = -1/2 sum_{0 < |i - j| <= kBandW} u_i b_ij (FP32), b_ij = conj(b_ji) for i > j.
+__global__ void __launch_bounds__(256) ref_band_apply(int n, const float* __restrict__ Urf,
+                                                      const float* __restrict__ Uif,
+                                                      const double2* __restrict__ Bband, float* __restrict__ dUr,
+                                                      float* __restrict__ dUi) {
+  __shared__ float2 coef[2 * kBandW];
+  __shared__ int col[2 * kBandW];
+  const int j = blockIdx.y;
+  const long m = 2L * n;
+  if (threadIdx.x < 2 * kBandW) {
+    const int t = threadIdx.x;
+    int i;
+    double2 b;
+    if (t < kBandW) {  // i = j - 1 - t < j: stored as B[i, j]
+      i = j - 1 - t;
+      b = i >= 0 ? Bband[(long)j * kBandW + t] : make_double2(0.0, 0.0);
+    } else {  // i = j + 1 + (t - kBandW) > j: b_ij = conj(B[j, i])
+      const int q = t - kBandW;
+      i = j + 1 + q;
+      b = i < n ? Bband[(long)i * kBandW + q] : make_double2(0.0, 0.0);
+      b.y = -b.y;
+    }
+    col[t] = (i >= 0 && i < n) ? i : j;
+    coef[t] = (i >= 0 && i < n) ? make_float2((float)(-0.5 * b.x), (float)(-0.5 * b.y)) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (long r = (long)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (long)gridDim.x * blockDim.x) {
+    float sr = 0.f, si = 0.f;
+#pragma unroll 8
+    for (int t = 0; t < 2 * kBandW; ++t) {
+      const long c = (long)col[t] * m + r;
+      const float xr = Urf[c], xi = Uif[c];
+      const float2 e = coef[t];
+      sr = fmaf(xr, e.x, fmaf(-xi, e.y, sr));
+      si = fmaf(xr, e.y, fmaf(xi, e.x, si));
+    }
+    dUr[r + (long)j * m] = sr;
+    dUi[r + (long)j * m] = si;
+  }
+}
+
 int refine(int n, const double* M, double* lam, double* X, int max_sweeps, double tol, void* work, DevStatus* st,
            cudaStream_t s, int* sweeps_done, double* resid, double* dlam_last, double* dlam_first) {
   StatusScope ss(st);
@@ -621,13 +734,14 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     // a sweep moves the eigenvalues by <= 1e-12 (relative) they are settled
     const bool converged = (res <= res_target && (it > 0 && dl <= 1e-12));
     if (converged || it >= max_sweeps) {
-      // Final polish, no new M U: pairs closer than the first sweep's cluster level
-      // are re-solved by Rayleigh-Ritz on the current (U, P) -- the Newton sweeps
-      // leave their mutual coupling at ~residual / gap, invisible in the residual --
-      // and every column is rescaled to y^H x = 1 exactly.
+      // Final polish, no new M U. (1) Pairs closer than the first sweep's cluster
+      // level are re-solved by Rayleigh-Ritz on the current (U, P). (2) The band
+      // biorthogonalization removes the remaining couplings of nearby pairs
+      // (invisible in the residual). (3) Every column is rescaled to y^H x = 1.
       BSE_CUDA(cudaMemcpyAsync(hlam.data(), lam, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
       BSE_CUDA(cudaStreamSynchronize(s));
       find_clusters(hlam, fmin(kFinalTauCap, fmax(kFinalTauFloor, fmax(1e-13, 20.0 * dl_level))), clusters, cid);
+      BSE_CUDA(cudaMemcpyAsync(w.cid, cid.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
       if (!clusters.empty()) {
         BSE_CUDA(cudaMemcpyAsync(w.clus, clusters.data(), sizeof(int2) * clusters.size(), cudaMemcpyHostToDevice, s));
         kcount(1);
@@ -635,14 +749,32 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
         BSE_LAUNCH_CHECK();
       }
       BSE_CUDA(cudaMemsetAsync(w.maxes, 0, 16, s));
+      kcount(1);
+      ref_colstats<<<n, 256, 0, s>>>(n, w.Ur, w.Ui, w.Pr, w.Pi, w.Urf, w.Uif, w.Rrf, w.Rif, lam, w.lam_new, w.bnorm,
+                                     w.scal, w.maxes);
+      BSE_LAUNCH_CHECK();
+      BSE_CUDA(cudaMemcpyAsync(lam, w.lam_new, 8 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+      BSE_CUDA(cudaMemcpyAsync(hm, w.maxes, 16, cudaMemcpyDeviceToHost, s));
+      // band biorthogonalization from the U copies ref_colstats just wrote
+      {
+        double2* Bband = w.Bband;
+        kcount(3);
+        ref_band_gram<<<dim3(n, kBandW / kBandChunk), 256, 0, s>>>(n, w.Ur, w.Ui, Bband);
+        BSE_LAUNCH_CHECK();
+        ref_band_apply<<<dim3(ceil_div(m, 256 * 8), n), 256, 0, s>>>(n, w.Urf, w.Uif, Bband, w.dUr, w.dUi);
+        BSE_LAUNCH_CHECK();
+        ref_apply<<<1024, 256, 0, s>>>((long)m * n, w.Ur, w.Ui, w.dUr, w.dUi);
+        BSE_LAUNCH_CHECK();
+      }
+      // bnorm of the corrected columns (the Rayleigh quotients it also writes are
+      // not used: P is not updated by the correction)
       kcount(2);
       ref_colstats<<<n, 256, 0, s>>>(n, w.Ur, w.Ui, w.Pr, w.Pi, w.Urf, w.Uif, w.Rrf, w.Rif, lam, w.lam_new, w.bnorm,
                                      w.scal, w.maxes);
       BSE_LAUNCH_CHECK();
       ref_normalize<<<dim3(ceil_div(m, 256 * 4), n), 256, 0, s>>>(n, w.Ur, w.Ui, w.bnorm);
       BSE_LAUNCH_CHECK();
-      BSE_CUDA(cudaMemcpyAsync(lam, w.lam_new, 8 * (size_t)n, cudaMemcpyDeviceToDevice, s));
-      BSE_CUDA(cudaMemcpyAsync(hm, w.maxes, 16, cudaMemcpyDeviceToHost, s));
+      // the host vectors must outlive the asynchronous uploads above
       BSE_CUDA(cudaStreamSynchronize(s));
       memcpy(&res, &hm[0], 8);
       if (verbose) fprintf(stderr, "[bse refine] n=%d final: %zu clusters, max scaled residual %.3e\n", n,

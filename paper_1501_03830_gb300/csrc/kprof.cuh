@@ -26,6 +26,9 @@ enum KClass {
   K_ELEMENTWISE,
   K_GEMM_TC,
   K_GEMM_TF32,
+  K_SBR_QR,     // band reduction: panel QR
+  K_SBR_CHASE,  // band reduction: bulge chasing
+  K_SBR_Q2,     // band reduction: back-transform of the chase
   K_NUM_CLASSES
 };
 

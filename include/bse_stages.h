@@ -58,6 +58,39 @@ size_t bse_stage_tridiag_worksize(int m, int fp32);
 int bse_stage_tridiag(int m, void* W, int ldw, double* e, void* tau, int fp32, void* work, int* dev_status,
                       void* stream);
 
+/* Two-stage (successive band) form of Algorithm 3 step 1 for FP32 W (Section 3.3,
+ * closing remark: band reduction in place of the memory-bound skew SYMV). m >= 3;
+ * W: m x m FP32, strict lower triangle read, leading dimension ldw divisible by 32
+ * and a 16-byte aligned base (else BSE_ERR_ARG); W's upper triangle is used.
+ * Stage 1 (dense -> half-bandwidth 64, panel QR plus tensor-core two-sided
+ * updates) leaves, for every column k, the reflector v_k with its unit entry
+ * written at row k+64 in W[k+64:m, k] and its scalar in tau[k] (FP32, m entries;
+ * zero where there is none); stage 2 (bulge chasing) leaves its reflectors in
+ * `work` (size bse_stage_sbr_worksize(m), owned by the caller) for
+ * bse_stage_sbr_apply_q2 / bse_stage_sbr_backtransform. On return e[k] = T[k+1, k]
+ * (FP64, k = 0..m-2, e[m-1] = 0) with W = Q T Q^T, Q = Q1 Q2, Q e_1 = e_1, so |e|
+ * equals |e| of bse_stage_tridiag in exact arithmetic (implicit-Q theorem). Both
+ * stages' bounded waits store BSE_ERR_TIMEOUT in dev_status instead of hanging. */
+size_t bse_stage_sbr_worksize(int m);
+int bse_stage_sbr(int m, float* W, int ldw, double* e, float* tau, void* work, int* dev_status, void* stream);
+
+/* Phi <- Phi Q2 (m x m FP32, column-major, leading dimension ldp >= m) with the
+ * stage-2 reflectors that the last bse_stage_sbr left in `work`. */
+int bse_stage_sbr_apply_q2(int m, float* Phi, int ldp, void* work, void* stream);
+
+/* Algorithm 3 steps 3-6 after bse_stage_sbr: Phi = L Q1 Q2 in place of L (FP32,
+ * lower triangle of L read), then X, Y as bse_stage_backtransform (fp32 = 1) makes
+ * them. bt_work: bse_stage_backtransform_worksize(m, 1) bytes; sbr_work: the
+ * workspace of the bse_stage_sbr call that reduced this W. */
+int bse_stage_sbr_backtransform(int m, float* L, int ldl, const float* W, int ldw, const float* tau,
+                                const double* Vs, const double* lam, double* X, double* Y, int ldx, void* bt_work,
+                                void* sbr_work, void* stream);
+
+/* Order m = 2n from which the mixed paths of bse_solve (and of the batched and
+ * serving calls) use the two-stage reduction instead of the one-stage one
+ * (default 2048; 0 = never). Process-wide; set it before solving. */
+int bse_set_band_reduction(int min_m);
+
 /* Diagnostics of the tridiagonal reduction (no counterpart in the paper):
  * bse_debug_trace_tridiag makes every later bse_stage_tridiag / bse_solve record,
  * for columns j < `columns`, the device clock (ns) of each block at five points

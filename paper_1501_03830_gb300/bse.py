@@ -48,6 +48,8 @@ EXPORTS = [
     "bse_stage_refine_worksize", "bse_stage_refine", "bse_tc_gemm_bf16", "bse_ozaki_worksize", "bse_ozaki_gemm",
     "bse_ozaki_digit_bits",
     "bse_tc32_gemm", "bse_set_fp32_gemm",
+    "bse_stage_sbr_worksize", "bse_stage_sbr", "bse_stage_sbr_apply_q2", "bse_stage_sbr_backtransform",
+    "bse_set_band_reduction",
 ]
 
 
@@ -136,6 +138,11 @@ def lib() -> C.CDLL:
         "bse_ozaki_gemm": (i, [i, i, i, vp, i, vp, i, vp, i, i, vp, vp, vp]),
         "bse_tc32_gemm": (i, [i, i, i, C.c_float, vp, i, i, vp, i, i, C.c_float, vp, i, i, i, vp, vp]),
         "bse_set_fp32_gemm": (i, [i]),
+        "bse_stage_sbr_worksize": (sz, [i]),
+        "bse_stage_sbr": (i, [i, vp, i, vp, vp, vp, vp, vp]),
+        "bse_stage_sbr_apply_q2": (i, [i, vp, i, vp, vp]),
+        "bse_stage_sbr_backtransform": (i, [i, vp, i, vp, i, vp, vp, vp, vp, vp, i, vp, vp, vp]),
+        "bse_set_band_reduction": (i, [i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -26,9 +26,19 @@ int tdeig(int m, const double* e, double* lam, double* Vs, double* work, DevStat
 
 template <typename T>
 size_t bt_worksize(int m);
+// Phi = L U from the reflectors in W (reflector j starts at row j + off), then
+// (with sbr_work, the band reduction's workspace) Phi <- Phi Q2, then X, Y.
 template <typename T>
 int backtransform(int m, T* L, long ldl, const T* W, long ldw, const T* tau, const double* Vs, const double* lam,
-                  double* X, double* Y, long ldx, void* work, cudaStream_t s);
+                  double* X, double* Y, long ldx, void* work, cudaStream_t s, int off = 1, void* sbr_work = nullptr);
+
+// two-stage (band) reduction of the FP32 skew W (k_sbr.cu): e = T's sub-diagonal,
+// stage-1 reflectors in W below the band (explicit unit entries at rows j + b)
+// with scalars in tau; stage-2 reflectors kept in the workspace for sbr_apply_q2
+constexpr int kSbrBand = 64;  // half-bandwidth of the first stage (the off of its reflectors)
+size_t sbr_worksize(int m);
+int sbr_reduce(int m, float* W, long ldw, double* e, float* tau, void* work, DevStatus* st, cudaStream_t s);
+int sbr_apply_q2(int m, float* Phi, long ldp, void* work, cudaStream_t s);
 
 int weights(int n, const double* X, long ldx, const double* dr, const double* dl, double* w, cudaStream_t s);
 

@@ -78,16 +78,18 @@ static BtWork<T> carve_bt(void* work, int m) {
   return w;
 }
 
-// Panel of reflectors j0 .. j0+nbp-1 restricted to rows j0+1 .. m-1 (they are
-// zero above): Vb[r, t] = v_{j0+t}[j0+1+r] = W[j0+1+r, j0+t] for r >= t, else 0.
+// Panel of reflectors j0 .. j0+nbp-1 restricted to rows j0+off .. m-1 (reflector j
+// starts at row j+off with its explicit unit entry; off = 1 for Algorithm 3's
+// reduction, b for the band reduction's first stage): Vb[r, t] =
+// v_{j0+t}[j0+off+r] = W[j0+off+r, j0+t] for r >= t, else 0.
 template <typename T>
-__global__ void bt_copy_panel(int m, int j0, int nbp, const T* __restrict__ W, long ldw, T* __restrict__ Vb,
-                              long ldv) {
+__global__ void bt_copy_panel(int m, int j0, int off, int nbp, const T* __restrict__ W, long ldw,
+                              T* __restrict__ Vb, long ldv) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
   if (r >= ldv) return;
   T v = T(0);
-  if (t < nbp && r >= t && j0 + 1 + r < m) v = W[j0 + 1 + r + (long)(j0 + t) * ldw];
+  if (t < nbp && r >= t && j0 + off + r < m) v = W[j0 + off + r + (long)(j0 + t) * ldw];
   Vb[r + (long)t * ldv] = v;
 }
 
@@ -195,7 +197,8 @@ __global__ void bt_epilogue(int n, const T* __restrict__ Fre, const T* __restric
 
 template <typename T>
 int backtransform(int m, T* L, long ldl, const T* W, long ldw, const T* tau, const double* Vs,
-                  const double* lam, double* X, double* Y, long ldx, void* work, cudaStream_t s) {
+                  const double* lam, double* X, double* Y, long ldx, void* work, cudaStream_t s, int off,
+                  void* sbr_work) {
   const int n = m / 2;
   BtWork<T> w = carve_bt<T>(work, m);
   {
@@ -203,14 +206,14 @@ int backtransform(int m, T* L, long ldl, const T* W, long ldw, const T* tau, con
     bt_zero_upper<T><<<dim3(ceil_div(m, 256), m), 256, 0, s>>>(m, L, ldl);
   }
   BSE_LAUNCH_CHECK();
-  const int nref = m - 1;  // reflectors j = 0..m-2 act on rows/cols j+1..m-1
+  const int nref = m - off;  // reflectors j = 0..m-off-1 act on rows/cols j+off..m-1
   const long ldv = w.ldv;
   for (int j0 = 0; j0 < nref; j0 += BT_NB) {
     const int nbp = min(BT_NB, nref - j0);
-    const int rows = m - j0 - 1;
+    const int rows = m - j0 - off;
     {
       KprofScope ks(K_ELEMENTWISE, s, 2.0 * sizeof(T) * rows * BT_NB, 0.0);
-      bt_copy_panel<T><<<dim3(ceil_div(ldv, 256), BT_NB), 256, 0, s>>>(m, j0, nbp, W, ldw, w.Vb, ldv);
+      bt_copy_panel<T><<<dim3(ceil_div(ldv, 256), BT_NB), 256, 0, s>>>(m, j0, off, nbp, W, ldw, w.Vb, ldv);
     }
     BSE_LAUNCH_CHECK();
     // G = V^T V
@@ -230,12 +233,14 @@ int backtransform(int m, T* L, long ldl, const T* W, long ldw, const T* tau, con
       bt_larft<T><<<1, BT_NB, 0, s>>>(nbp, w.G, tau + j0, w.Tf);
     }
     BSE_LAUNCH_CHECK();
-    T* Phi = L + (long)(j0 + 1) * ldl;  // columns j0+1..m-1
+    T* Phi = L + (long)(j0 + off) * ldl;  // columns j0+off..m-1
     // Z = Phi V ; Z2 = Z T ; Phi -= Z2 V^T
     BSE_TRY(gemm<T>(m, nbp, rows, 1.0, Phi, ldl, false, w.Vb, ldv, false, 0.0, w.Z, ldv, s));
     BSE_TRY(gemm<T>(m, nbp, nbp, 1.0, w.Z, ldv, false, w.Tf, BT_NB, false, 0.0, w.Z2, ldv, s, TRI_NONE, TRI_UPPER));
     BSE_TRY(gemm<T>(m, rows, nbp, -1.0, w.Z2, ldv, false, w.Vb, ldv, true, 1.0, Phi, ldl, s));
   }
+  // the band reduction's second stage: Phi <- Phi Q2
+  if (sbr_work) BSE_TRY(sbr_apply_q2(m, reinterpret_cast<float*>(L), ldl, sbr_work, s));
   const T* Vsx;
   long ldvs = n;
   if (sizeof(T) == 4) {
@@ -277,9 +282,9 @@ int backtransform(int m, T* L, long ldl, const T* W, long ldw, const T* tau, con
 template size_t bt_worksize<double>(int);
 template size_t bt_worksize<float>(int);
 template int backtransform<double>(int, double*, long, const double*, long, const double*, const double*,
-                                   const double*, double*, double*, long, void*, cudaStream_t);
+                                   const double*, double*, double*, long, void*, cudaStream_t, int, void*);
 template int backtransform<float>(int, float*, long, const float*, long, const float*, const double*,
-                                  const double*, double*, double*, long, void*, cudaStream_t);
+                                  const double*, double*, double*, long, void*, cudaStream_t, int, void*);
 
 }  // namespace bse
 
@@ -294,7 +299,7 @@ extern "C" int bse_stage_backtransform(int m, void* L, int ldl, const void* W, i
     return BSE_ERR_ARG;
   if (fp32)
     return bse::backtransform<float>(m, (float*)L, ldl, (const float*)W, ldw, (const float*)tau, Vs, lam, X, Y, ldx,
-                                     work, (cudaStream_t)stream);
+                                     work, (cudaStream_t)stream, 1, nullptr);
   return bse::backtransform<double>(m, (double*)L, ldl, (const double*)W, ldw, (const double*)tau, Vs, lam, X, Y,
-                                    ldx, work, (cudaStream_t)stream);
+                                    ldx, work, (cudaStream_t)stream, 1, nullptr);
 }

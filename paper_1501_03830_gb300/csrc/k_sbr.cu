@@ -40,6 +40,7 @@ namespace bse {
 
 constexpr int SBR_B = 64;     // half-bandwidth after stage 1
 constexpr int QR_RB = 128;    // panel rows per thread block of the panel QR
+constexpr int GRAM_RB = 64;   // rows per thread block of the tall-skinny Gram kernel
 constexpr int SBR_LDB = 2 * SBR_B + 1;  // compact band: rows j .. j+2b of column j
 constexpr long kSbrSpin = 1L << 25;     // polls before a wait gives up (~2 s)
 
@@ -54,7 +55,7 @@ struct SbrWork {
   float* YV;      // ldv x 2b: [Y | -V]
   float* X;       // ldv x b
   float *G, *S, *Z, *Tf;  // b x b
-  double* Gpart;  // ceil(m / QR_RB) x b x b partial Gram matrices
+  double* Gpart;  // ceil(m / GRAM_RB) x b x b partial Gram matrices
   double* qpart;  // [2][grid][b + 1] panel-QR partial sums
   double* rowq;   // [2][b] pivot rows of the panel QR
   unsigned* bar;  // grid barrier words (panel QR)
@@ -62,20 +63,26 @@ struct SbrWork {
   float* V2;      // Kmax x m x b reflectors of stage 2
   float* tau2;    // Kmax x m
   int* progress;  // m: completed steps per sweep
+  float* Tq;      // b x b triangular factor per back-transform block of stage 2
   long ldv;
   int kmax;
 };
 
+size_t sbr_q2_blocks(int m);
+static_assert(SBR_B == kSbrBand, "band width");
+
 size_t sbr_worksize(int m) {
   const size_t ldv = ld32(m), kmax = sbr_steps(m, 0) + 1, grid = (m + QR_RB - 1) / QR_RB + 1;
+  const size_t gparts = (m + GRAM_RB - 1) / GRAM_RB + 1;
   size_t b = 0;
   b += 2 * al256s(4 * ldv * 2 * SBR_B) + al256s(4 * ldv * SBR_B);
   b += 4 * al256s(4 * SBR_B * SBR_B);
-  b += al256s(8 * grid * SBR_B * SBR_B);
+  b += al256s(8 * gparts * SBR_B * SBR_B);
   b += al256s(8 * 2 * grid * (SBR_B + 1)) + al256s(8 * 2 * SBR_B) + al256s(64);
   b += al256s(4 * (size_t)SBR_LDB * m);
   b += al256s(4 * kmax * (size_t)m * SBR_B) + al256s(4 * kmax * (size_t)m);
   b += al256s(4 * (size_t)m);
+  b += al256s(4 * sbr_q2_blocks(m) * SBR_B * SBR_B);
   return b;
 }
 
@@ -97,7 +104,7 @@ static SbrWork carve_sbr(void* work, int m) {
   w.S = (float*)take(4 * SBR_B * SBR_B);
   w.Z = (float*)take(4 * SBR_B * SBR_B);
   w.Tf = (float*)take(4 * SBR_B * SBR_B);
-  w.Gpart = (double*)take(8 * grid * SBR_B * SBR_B);
+  w.Gpart = (double*)take(8 * ((m + GRAM_RB - 1) / GRAM_RB + 1) * SBR_B * SBR_B);
   w.qpart = (double*)take(8 * 2 * grid * (SBR_B + 1));
   w.rowq = (double*)take(8 * 2 * SBR_B);
   w.bar = (unsigned*)take(64);
@@ -105,6 +112,7 @@ static SbrWork carve_sbr(void* work, int m) {
   w.V2 = (float*)take(4 * (size_t)w.kmax * m * SBR_B);
   w.tau2 = (float*)take(4 * (size_t)w.kmax * m);
   w.progress = (int*)take(4 * (size_t)m);
+  w.Tq = (float*)take(4 * sbr_q2_blocks(m) * SBR_B * SBR_B);
   return w;
 }
 
@@ -180,16 +188,16 @@ __global__ void sbr_mirror(int m, float* __restrict__ W, long ldw) {
   }
 }
 
-// Partial A^T B over 128-row blocks (A, B: rows x b, FP32), in FP64 per block;
+// Partial A^T B over GRAM_RB-row blocks (A, B: rows x b, FP32), in FP64 per block;
 // sbr_gram_sum adds the partials in block order (deterministic).
 __global__ void __launch_bounds__(256) sbr_gram_part(int rows, const float* __restrict__ A, long lda,
                                                      const float* __restrict__ B, long ldb,
                                                      double* __restrict__ part) {
-  __shared__ float sA[QR_RB][SBR_B + 1];
-  __shared__ float sB[QR_RB][SBR_B + 1];
-  const int r0 = blockIdx.x * QR_RB;
-  for (int e = threadIdx.x; e < QR_RB * SBR_B; e += 256) {
-    const int r = e % QR_RB, c = e / QR_RB;
+  __shared__ float sA[GRAM_RB][SBR_B + 1];
+  __shared__ float sB[GRAM_RB][SBR_B + 1];
+  const int r0 = blockIdx.x * GRAM_RB;
+  for (int e = threadIdx.x; e < GRAM_RB * SBR_B; e += 256) {
+    const int r = e % GRAM_RB, c = e / GRAM_RB;
     const bool ok = r0 + r < rows;
     sA[r][c] = ok ? A[r0 + r + (long)c * lda] : 0.f;
     sB[r][c] = ok ? B[r0 + r + (long)c * ldb] : 0.f;
@@ -199,7 +207,7 @@ __global__ void __launch_bounds__(256) sbr_gram_part(int rows, const float* __re
   double acc[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) acc[q] = 0.0;
-  for (int r = 0; r < QR_RB; ++r) {
+  for (int r = 0; r < GRAM_RB; ++r) {
     const double a = sA[r][i];
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q] = fma(a, (double)sB[r][jb + 4 * q], acc[q]);
@@ -219,7 +227,7 @@ __global__ void sbr_gram_sum(int parts, const double* __restrict__ part, float* 
 
 static int gram(int rows, const float* A, long lda, const float* B, long ldb, double* part, float* G,
                 cudaStream_t s) {
-  const int parts = ceil_div(rows, QR_RB);
+  const int parts = ceil_div(rows, GRAM_RB);
   KprofScope ks(K_ELEMENTWISE, s, 8.0 * rows * (double)SBR_B, 4.0 * rows * (double)SBR_B * SBR_B);
   sbr_gram_part<<<parts, 256, 0, s>>>(rows, A, lda, B, ldb, part);
   BSE_LAUNCH_CHECK();
@@ -619,4 +627,322 @@ __global__ void __launch_bounds__(256) sbr_chase(ChaseArgs a) {
       }
     }
   }
+}
+
+// ---- back-transform of stage 2: Phi <- Phi Q2 ---------------------------------------
+// The reflectors H_{j,k} of QG = b consecutive sweeps j in [g b, g b + b) at one
+// step k act on the windows [j+1+kb, j+(k+1)b], shifted by one per sweep: as a
+// block they are I - V T V^T with V the (2b-1) x b "parallelogram" (column t is
+// v_{gb+t,k} at rows t .. t+b-1 of the block's window [gb+1+kb, gb+(k+2)b-1)).
+// H_{j,k} must follow H_{j-1,k} and H_{j-1,k+1} (they overlap) and commutes with
+// everything it does not overlap, so applying the blocks group by group
+// (g ascending) with k descending inside a group reproduces the product Q2 of the
+// sequential order. The rows of Phi are independent: one thread block per slab of
+// QR_RB rows applies every block to its slab, window columns in shared memory.
+constexpr int Q2_RS = 128;  // rows of Phi per slab
+
+__host__ __device__ inline int q2_groups(int m) { return (m - 2 + SBR_B - 1) / SBR_B; }
+__host__ __device__ inline int q2_kmax(int m, int g) { return (g * SBR_B <= m - 3) ? sbr_steps(m, g * SBR_B) : 0; }
+
+size_t sbr_q2_blocks(int m) {
+  size_t t = 0;
+  for (int g = 0; g < q2_groups(m); ++g) t += q2_kmax(m, g);
+  return t;
+}
+
+// T factor of block (g, k) (grid: groups x Kmax; blocks with k >= kmax_g exit)
+__global__ void __launch_bounds__(SBR_B) sbr_q2_prep(int m, const float* __restrict__ V2,
+                                                     const float* __restrict__ tau2, float* __restrict__ Tq) {
+  __shared__ float Vc[SBR_B][SBR_B + 1];  // Vc[t][i] = v_{gb+t,k}[i] (window row t + i)
+  __shared__ float Ts[SBR_B][SBR_B + 1];
+  __shared__ float tau[SBR_B], gcol[SBR_B];
+  const int g = blockIdx.x, k = blockIdx.y, t = threadIdx.x;
+  if (k >= q2_kmax(m, g)) return;
+  long off = 0;
+  for (int h = 0; h < g; ++h) off += q2_kmax(m, h);
+  off += k;
+  {
+    const int j = g * SBR_B + t;
+    const bool has = j <= m - 3 && k < sbr_steps(m, j);
+    for (int i = 0; i < SBR_B; ++i) Vc[t][i] = has ? V2[((long)k * m + j) * SBR_B + i] : 0.f;
+    tau[t] = has ? tau2[(long)k * m + j] : 0.f;
+  }
+  for (int r = 0; r < SBR_B; ++r) Ts[r][t] = 0.f;
+  __syncthreads();
+  // column i of T: T[0:i, i] = -tau_i T[0:i, 0:i] (V^T v_i)[0:i]; v_t^T v_i over the
+  // common window rows i .. t+b-1 (t < i)
+  for (int i = 0; i < SBR_B; ++i) {
+    if (t < i) {
+      double acc = 0.0;
+      for (int q = i - t; q < SBR_B; ++q) acc = fma((double)Vc[t][q], (double)Vc[i][q - (i - t)], acc);
+      gcol[t] = (float)(-(double)tau[i] * acc);
+    }
+    __syncthreads();
+    if (t < i) {
+      float sacc = 0.f;
+      for (int l = t; l < i; ++l) sacc = fmaf(Ts[t][l], gcol[l], sacc);
+      Ts[t][i] = sacc;
+    }
+    if (t == 0) Ts[i][i] = tau[i];
+    __syncthreads();
+  }
+  float* out = Tq + off * SBR_B * SBR_B;
+  for (int r = 0; r < SBR_B; ++r) out[r + t * SBR_B] = Ts[r][t];
+}
+
+constexpr int Q2_LDR = Q2_RS + 4;  // shared row pitch of the window and Z buffers
+constexpr int Q2_SLOTS = 128;      // window columns held (a block window is at most 2b - 1 wide)
+constexpr size_t Q2_SMEM = sizeof(float) * ((size_t)Q2_SLOTS * Q2_LDR + 2 * SBR_B * (SBR_B + 1) + 2 * SBR_B * Q2_LDR);
+
+__device__ __forceinline__ void q2_move(int m, float* __restrict__ Phi, long ldp, float* ring, int r0, int rows,
+                                        int c_lo, int c_hi, bool store) {
+  // columns [c_lo, c_hi) between Phi[r0 .. r0+rows) and their ring slots
+  const int ncol = c_hi - c_lo;
+  for (int e = threadIdx.x; e < ncol * Q2_RS; e += blockDim.x) {
+    const int r = e % Q2_RS, c = c_lo + e / Q2_RS;
+    if (r >= rows) continue;
+    float* sp = ring + (size_t)(c % Q2_SLOTS) * Q2_LDR + r;
+    float* gp = Phi + r0 + r + (long)c * ldp;
+    if (store) *gp = *sp;
+    else *sp = *gp;
+  }
+}
+
+__global__ void __launch_bounds__(256) sbr_q2_apply(int m, float* __restrict__ Phi, long ldp,
+                                                    const float* __restrict__ V2, const float* __restrict__ Tq) {
+  extern __shared__ __align__(16) float q2s[];
+  float* ring = q2s;                                   // [slot][row]
+  float (*Vc)[SBR_B + 1] = reinterpret_cast<float (*)[SBR_B + 1]>(ring + (size_t)Q2_SLOTS * Q2_LDR);
+  float (*Ts)[SBR_B + 1] = Vc + SBR_B;
+  float* Zs = reinterpret_cast<float*>(Ts + SBR_B);    // [t][row]
+  float* Z2s = Zs + SBR_B * Q2_LDR;
+  const int tid = threadIdx.x;
+  const int r0 = blockIdx.x * Q2_RS, rows = min(Q2_RS, m - r0);
+  const int rt = tid & 15, tt = tid >> 4;  // 8-row tile, 4-column (Z) or 8-column (update) tile
+  int lo = 0, hi = 0;                       // window columns held in the ring
+  long off = 0;
+  const int NG = q2_groups(m);
+  for (int g = 0; g < NG; ++g) {
+    const int K = q2_kmax(m, g);
+    for (int k = K - 1; k >= 0; --k) {
+      const int s0 = g * SBR_B + 1 + k * SBR_B;
+      const int wc = min(2 * SBR_B - 1, m - s0);
+      // ring: write back what leaves, read what enters
+      q2_move(m, Phi, ldp, ring, r0, rows, max(lo, s0 + wc), hi, true);
+      q2_move(m, Phi, ldp, ring, r0, rows, lo, min(hi, s0), true);
+      __syncthreads();
+      const int keep_lo = max(lo, s0), keep_hi = min(hi, s0 + wc);
+      if (keep_lo < keep_hi) {
+        q2_move(m, Phi, ldp, ring, r0, rows, s0, keep_lo, false);
+        q2_move(m, Phi, ldp, ring, r0, rows, keep_hi, s0 + wc, false);
+      } else {
+        q2_move(m, Phi, ldp, ring, r0, rows, s0, s0 + wc, false);
+      }
+      lo = s0;
+      hi = s0 + wc;
+      // the block's reflectors and T
+      for (int e = tid; e < SBR_B * SBR_B; e += 256) {
+        const int t = e / SBR_B, i = e % SBR_B;
+        const int j = g * SBR_B + t;
+        const bool has = j <= m - 3 && k < sbr_steps(m, j);
+        Vc[t][i] = has ? __ldg(V2 + ((long)k * m + j) * SBR_B + i) : 0.f;
+        Ts[i][t] = __ldg(Tq + (off + k) * SBR_B * SBR_B + i + t * SBR_B);
+      }
+      __syncthreads();
+      // Z = Phi_w V (rows x b): column t of V is v_t at window rows t .. t+b-1
+      {
+        float acc[8][4];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[u][q] = 0.f;
+        const int t0 = 4 * tt;
+        const int cend = min(t0 + 3 + SBR_B, wc);
+        for (int c = t0; c < cend; ++c) {
+          const float* col = ring + (size_t)((s0 + c) % Q2_SLOTS) * Q2_LDR + 8 * rt;
+          float ph[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) ph[u] = col[u];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = c - (t0 + q);
+            const float vv = (i >= 0 && i < SBR_B) ? Vc[t0 + q][i] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u][q] = fmaf(ph[u], vv, acc[u][q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int u = 0; u < 8; ++u) Zs[(t0 + q) * Q2_LDR + 8 * rt + u] = acc[u][q];
+      }
+      __syncthreads();
+      // Z2 = Z T (T upper triangular)
+      {
+        float acc[8][4];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[u][q] = 0.f;
+        const int t0 = 4 * tt;
+        for (int s = 0; s < t0 + 4; ++s) {
+          float z[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) z[u] = Zs[s * Q2_LDR + 8 * rt + u];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float tv = (s <= t0 + q) ? Ts[s][t0 + q] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u][q] = fmaf(z[u], tv, acc[u][q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int u = 0; u < 8; ++u) Z2s[(t0 + q) * Q2_LDR + 8 * rt + u] = acc[u][q];
+      }
+      __syncthreads();
+      // Phi_w -= Z2 V^T: window column c gets sum over t with 0 <= c - t < b
+      {
+        float acc[8][8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+        const int c0 = 8 * tt;
+        const int tlo = max(0, c0 - SBR_B + 1), thi = min(SBR_B - 1, c0 + 7);
+        for (int t = tlo; t <= thi; ++t) {
+          float z[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) z[u] = Z2s[t * Q2_LDR + 8 * rt + u];
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            const int i = c0 + v - t;
+            const float vv = (i >= 0 && i < SBR_B) ? Vc[t][i] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u][v] = fmaf(z[u], vv, acc[u][v]);
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          const int c = c0 + v;
+          if (c < wc) {
+            float* col = ring + (size_t)((s0 + c) % Q2_SLOTS) * Q2_LDR + 8 * rt;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) col[u] -= acc[u][v];
+          }
+        }
+      }
+      __syncthreads();
+    }
+    off += K;
+  }
+  q2_move(m, Phi, ldp, ring, r0, rows, lo, hi, true);
+}
+
+// ---- host drivers ---------------------------------------------------------------------
+
+static long g_sbr_spin = kSbrSpin;
+
+int sbr_reduce(int m, float* W, long ldw, double* e, float* tau, void* work, DevStatus* st, cudaStream_t s) {
+  StatusScope ss(st);
+  if (m < 3) {
+    record_message("band reduction needs m >= 3");
+    return BSE_ERR_ARG;
+  }
+  SbrWork w = carve_sbr(work, m);
+  BSE_TRY(sbr_stage1(m, W, ldw, tau, w, st, s));
+  {
+    KprofScope ks(K_ELEMENTWISE, s, 4.0 * (SBR_B + SBR_LDB) * (double)m, 0.0);
+    sbr_extract_band<<<m, 128, 0, s>>>(m, W, ldw, w.band);
+  }
+  BSE_LAUNCH_CHECK();
+  {
+    KprofScope ks(K_ELEMENTWISE, s, 8.0 * m, 0.0);
+    sbr_unit_diag<<<ceil_div(m, 256), 256, 0, s>>>(m, W, ldw);
+  }
+  BSE_LAUNCH_CHECK();
+  BSE_CUDA(cudaMemsetAsync(w.progress, 0, sizeof(int) * (size_t)m, s));
+  BSE_CUDA(cudaMemsetAsync(w.V2, 0, sizeof(float) * (size_t)w.kmax * m * SBR_B, s));
+  BSE_CUDA(cudaMemsetAsync(w.tau2, 0, sizeof(float) * (size_t)w.kmax * m, s));
+  int dev = 0, nsm = 0, per_sm = 0;
+  BSE_CUDA(cudaGetDevice(&dev));
+  BSE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sbr_chase, 256, 0));
+  if (per_sm < 1) {
+    record_message("bulge-chasing kernel cannot be resident");
+    return BSE_ERR_CUDA;
+  }
+  ChaseArgs ca;
+  ca.m = m; ca.band = w.band; ca.V2 = w.V2; ca.tau2 = w.tau2; ca.progress = w.progress; ca.st = st;
+  ca.spin = g_sbr_spin;
+  const int grid = max(1, min(nsm, m - 2));
+  {
+    // charged: the steps' 16 b^2 flops (left, right and two-sided applications), no HBM bytes
+    double steps = 0.0;
+    for (int j = 0; j + 2 < m; ++j) steps += sbr_steps(m, j);
+    KprofScope ks(K_SBR_CHASE, s, 0.0, 16.0 * SBR_B * SBR_B * steps);
+    void* args[] = {&ca};
+    BSE_CUDA(cudaLaunchCooperativeKernel((const void*)sbr_chase, dim3(grid), dim3(256), args, 0, s));
+  }
+  {
+    KprofScope ks(K_ELEMENTWISE, s, 12.0 * m, 0.0);
+    sbr_subdiag<<<ceil_div(m, 256), 256, 0, s>>>(m, w.band, e);
+  }
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
+int sbr_apply_q2(int m, float* Phi, long ldp, void* work, cudaStream_t s) {
+  SbrWork w = carve_sbr(work, m);
+  const int NG = q2_groups(m);
+  {
+    KprofScope ks(K_ELEMENTWISE, s, 0.0, 0.0);
+    sbr_q2_prep<<<dim3(NG, w.kmax), SBR_B, 0, s>>>(m, w.V2, w.tau2, w.Tq);
+  }
+  BSE_LAUNCH_CHECK();
+  static cudaError_t attr_err =
+      cudaFuncSetAttribute(sbr_q2_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Q2_SMEM);
+  if (attr_err != cudaSuccess) {
+    record_error("cudaFuncSetAttribute(sbr_q2_apply)", attr_err, __FILE__, __LINE__);
+    return BSE_ERR_CUDA;
+  }
+  {
+    // charged: 2 m^3-type flops of the reflectors (4 b flops per reflector and row), Phi read and written once
+    double refl = 0.0;
+    for (int j = 0; j + 2 < m; ++j) refl += sbr_steps(m, j);
+    KprofScope ks(K_SBR_Q2, s, 8.0 * (double)m * m, 4.0 * SBR_B * (double)m * refl);
+    sbr_q2_apply<<<ceil_div(m, Q2_RS), 256, Q2_SMEM, s>>>(m, Phi, ldp, w.V2, w.Tq);
+  }
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
+}  // namespace bse
+
+extern "C" size_t bse_stage_sbr_worksize(int m) { return m >= 3 ? bse::sbr_worksize(m) : 0; }
+
+extern "C" int bse_stage_sbr(int m, float* W, int ldw, double* e, float* tau, void* work, int* dev_status,
+                             void* stream) {
+  if (m < 3 || !W || ldw < m || !e || !tau || !work || !dev_status) return BSE_ERR_ARG;
+  if ((ldw % 32) != 0 || (reinterpret_cast<uintptr_t>(W) % 16) != 0) {
+    bse::record_message("bse_stage_sbr: W needs a 16-byte aligned base and a leading dimension divisible by 32");
+    return BSE_ERR_ARG;
+  }
+  return bse::sbr_reduce(m, W, ldw, e, tau, work, reinterpret_cast<bse::DevStatus*>(dev_status),
+                         (cudaStream_t)stream);
+}
+
+extern "C" int bse_stage_sbr_apply_q2(int m, float* Phi, int ldp, void* work, void* stream) {
+  if (m < 3 || !Phi || ldp < m || !work) return BSE_ERR_ARG;
+  return bse::sbr_apply_q2(m, Phi, ldp, work, (cudaStream_t)stream);
+}
+
+extern "C" int bse_stage_sbr_backtransform(int m, float* L, int ldl, const float* W, int ldw, const float* tau,
+                                           const double* Vs, const double* lam, double* X, double* Y, int ldx,
+                                           void* bt_work, void* sbr_work, void* stream) {
+  if (m < 4 || (m & 1) || !L || !W || !tau || !Vs || !lam || ldl < m || ldw < m || ldx < m || !bt_work || !sbr_work)
+    return BSE_ERR_ARG;
+  return bse::backtransform<float>(m, L, ldl, W, ldw, tau, Vs, lam, X, Y, ldx, bt_work, (cudaStream_t)stream,
+                                   bse::kSbrBand, sbr_work);
 }

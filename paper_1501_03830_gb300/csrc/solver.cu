@@ -9,6 +9,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <chrono>
 #include <map>
 #include <mutex>
@@ -46,6 +47,13 @@ bool is_device_ptr(const void* p) {
 // columns stay aligned whatever n is.
 size_t w_ld(int n) { return ((2 * (size_t)n + 31) / 32) * 32; }
 
+static std::atomic<int> g_band_min_m{2048};
+
+bool use_band_reduction(int m, int precision) {
+  const int lim = g_band_min_m.load(std::memory_order_relaxed);
+  return precision != BSE_FP64 && lim > 0 && m >= lim && m >= 4;
+}
+
 size_t workspace_bytes(int n, int precision) {
   const size_t m = 2 * (size_t)n;
   const bool f32 = precision != BSE_FP64;
@@ -59,6 +67,7 @@ size_t workspace_bytes(int n, int precision) {
   b += al256(8 * m * n);                       // Vs
   b += 2 * al256(16 * m * n);                  // X, Y
   b += al256(64);                              // status
+  if (use_band_reduction((int)m, precision)) b += al256(sbr_worksize((int)m));
   size_t scratch = f32 ? potrf_worksize<float>((int)m) : potrf_worksize<double>((int)m);
   scratch = std::max(scratch, f32 ? trd_worksize<float>((int)m) : trd_worksize<double>((int)m));
   scratch = std::max(scratch, sizeof(double) * (m + 8));
@@ -106,6 +115,7 @@ void Workspace::carve(int n_) {
   X = (double*)take(16 * m * n);
   Y = (double*)take(16 * m * n);
   status = (DevStatus*)take(64);
+  sbr = use_band_reduction((int)m, precision) ? take(sbr_worksize((int)m)) : nullptr;
   scratch = p;
 }
 
@@ -175,6 +185,12 @@ extern "C" int bse_destroy(bse_ctx* c) {
 extern "C" int bse_set_stream(bse_ctx* c, void* stream) {
   if (!c) return BSE_ERR_ARG;
   c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+  return BSE_OK;
+}
+
+extern "C" int bse_set_band_reduction(int min_m) {
+  if (min_m < 0) return BSE_ERR_ARG;
+  bse::g_band_min_m.store(min_m);
   return BSE_OK;
 }
 
@@ -304,13 +320,18 @@ int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, co
     if (tm) cudaEventRecord(ev[2], s);
     BSE_TRY(form_W<float>(n, ws->Lf, ws->ldw, W, ws->ldw, s));
     if (tm) cudaEventRecord(ev[3], s);
-    BSE_TRY(tridiagonalize<float>(m, W, ws->ldw, ws->e, tau, ws->scratch, s, ws->status));
+    const bool band = ws->sbr != nullptr && use_band_reduction(m, precision);
+    if (band)
+      BSE_TRY(sbr_reduce(m, W, ws->ldw, ws->e, tau, ws->sbr, ws->status, s));
+    else
+      BSE_TRY(tridiagonalize<float>(m, W, ws->ldw, ws->e, tau, ws->scratch, s, ws->status));
     if (tm) cudaEventRecord(ev[4], s);
     BSE_TRY(tdeig(m, ws->e, ws->lam, ws->Vs, (double*)ws->scratch, ws->status, s));
     if (tm) cudaEventRecord(ev[5], s);
     const bool refine_now = precision == BSE_MIXED_REFINED;
     BSE_TRY(backtransform<float>(m, ws->Lf, ws->ldw, W, ws->ldw, tau, ws->Vs, ws->lam, ws->X,
-                                 (want_Y && !refine_now) ? ws->Y : nullptr, m, ws->scratch, s));
+                                 (want_Y && !refine_now) ? ws->Y : nullptr, m, ws->scratch, s,
+                                 band ? kSbrBand : 1, band ? ws->sbr : nullptr));
     if (tm) cudaEventRecord(ev[6], s);
     if (refine_now) {
       int sweeps = 0;

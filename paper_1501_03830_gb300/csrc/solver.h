@@ -26,6 +26,7 @@ struct Workspace {
   double* Vs = nullptr;               // sign-folded V+ (row-major m x n)
   double *X = nullptr, *Y = nullptr;  // complex128 2n x n
   DevStatus* status = nullptr;
+  void* sbr = nullptr;                // band reduction state kept from the reduction to the back-transform
   void* scratch = nullptr;            // stage scratch (max over stages)
   int init(int n, int precision);  // allocate workspace_bytes(n, precision) and carve it for n
   void carve(int n);               // lay the buffers out for n (workspace_bytes(n) <= bytes)
@@ -33,6 +34,8 @@ struct Workspace {
 };
 
 size_t workspace_bytes(int n, int precision);
+// the mixed paths reduce W in two stages (band, then tridiagonal) from this order m = 2n on
+bool use_band_reduction(int m, int precision);
 bool is_device_ptr(const void* p);
 
 struct ServeState;

@@ -88,7 +88,8 @@ int bse_stage_sbr_backtransform(int m, float* L, int ldl, const float* W, int ld
 
 /* Order m = 2n from which the mixed paths of bse_solve (and of the batched and
  * serving calls) use the two-stage reduction instead of the one-stage one
- * (default 2048; 0 = never). Process-wide; set it before solving. */
+ * (default 0 = never: measured slower than the one-stage panel on GB300 at
+ * n = 8192, see the design notes). Process-wide; set it before solving. */
 int bse_set_band_reduction(int min_m);
 
 /* Diagnostics of the tridiagonal reduction (no counterpart in the paper):

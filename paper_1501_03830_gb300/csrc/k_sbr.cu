@@ -188,8 +188,9 @@ __global__ void sbr_mirror(int m, float* __restrict__ W, long ldw) {
   }
 }
 
-// Partial A^T B over GRAM_RB-row blocks (A, B: rows x b, FP32), in FP64 per block;
-// sbr_gram_sum adds the partials in block order (deterministic).
+// Partial A^T B over GRAM_RB-row blocks (A, B: rows x b, FP32; FP32 sums of 64
+// terms per block); sbr_gram_sum adds the partials in FP64 in block order
+// (deterministic).
 __global__ void __launch_bounds__(256) sbr_gram_part(int rows, const float* __restrict__ A, long lda,
                                                      const float* __restrict__ B, long ldb,
                                                      double* __restrict__ part) {
@@ -204,17 +205,17 @@ __global__ void __launch_bounds__(256) sbr_gram_part(int rows, const float* __re
   }
   __syncthreads();
   const int i = threadIdx.x & 63, jb = threadIdx.x >> 6;  // output (i, jb + 4q)
-  double acc[16];
+  float acc[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+  for (int q = 0; q < 16; ++q) acc[q] = 0.f;
   for (int r = 0; r < GRAM_RB; ++r) {
-    const double a = sA[r][i];
+    const float a = sA[r][i];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = fma(a, (double)sB[r][jb + 4 * q], acc[q]);
+    for (int q = 0; q < 16; ++q) acc[q] = fmaf(a, sB[r][jb + 4 * q], acc[q]);
   }
   double* out = part + (size_t)blockIdx.x * SBR_B * SBR_B;
 #pragma unroll
-  for (int q = 0; q < 16; ++q) out[i + (jb + 4 * q) * SBR_B] = acc[q];
+  for (int q = 0; q < 16; ++q) out[i + (jb + 4 * q) * SBR_B] = (double)acc[q];
 }
 
 __global__ void sbr_gram_sum(int parts, const double* __restrict__ part, float* __restrict__ G) {
@@ -258,7 +259,8 @@ __global__ void sbr_make_yv(int N, const float* __restrict__ VY, float* __restri
 // Householder QR of the N x nc panel P (nc <= b), one cooperative launch: block g
 // keeps rows [g QR_RB, (g+1) QR_RB) in shared memory. For reflector q, every
 // block adds up, over its rows i > q, sigma = sum P[i,q]^2 and d_c = sum P[i,q] P[i,c]
-// (c > q) in FP64; the owner of row q publishes it. After one grid barrier every
+// (c > q) (FP32 over 32 rows, FP64 beyond: FP64 arithmetic is scarce on this
+// GPU); the owner of row q publishes it. After one grid barrier every
 // block sums the partials in block order (the same numbers everywhere), forms the
 // reflector (beta, tau, 1/(alpha - beta)) and w_c = v^T P[:, c] = P[q,c] +
 // d_c / (alpha - beta), and updates its rows: P[i,c] -= tau v_i w_c, P[i,q] = v_i.
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(256) sbr_panel_qr(QrArgs a) {
   __shared__ double sred[4][SBR_B];
   __shared__ double sdot[SBR_B];
   __shared__ double srow[SBR_B];
-  __shared__ double sw[SBR_B];
+  __shared__ float sw[SBR_B];
   __shared__ double sh[3];
   const int tid = threadIdx.x;
   const int i0 = blockIdx.x * QR_RB;
@@ -297,12 +299,12 @@ __global__ void __launch_bounds__(256) sbr_panel_qr(QrArgs a) {
     const int par = q & 1;
     double* part = a.part + (size_t)par * G * (SBR_B + 1);
     // partial sums over this block's rows i > q
-    double acc = 0.0;
+    float acc = 0.f;
     if (c >= q && c < a.nc) {
       const int rbeg = max(rg * 32, q + 1 - i0), rend = min(rg * 32 + 32, rows);
-      for (int r = rbeg; r < rend; ++r) acc = fma((double)sP[r][q], (double)sP[r][c], acc);
+      for (int r = rbeg; r < rend; ++r) acc = fmaf(sP[r][q], sP[r][c], acc);
     }
-    sred[rg][c] = acc;
+    sred[rg][c] = (double)acc;
     __syncthreads();
     if (tid < SBR_B) {
       const double t = (sred[0][tid] + sred[1][tid]) + (sred[2][tid] + sred[3][tid]);
@@ -327,8 +329,8 @@ __global__ void __launch_bounds__(256) sbr_panel_qr(QrArgs a) {
       if (blockIdx.x == 0) a.tau[q] = (float)h.tau;
     }
     __syncthreads();
-    const double tau = sh[1], scal = sh[2];
-    if (tid < SBR_B) sw[tid] = (tid > q && tid < a.nc) ? srow[tid] + scal * sdot[tid] : 0.0;
+    const float tau = (float)sh[1], scal = (float)sh[2];
+    if (tid < SBR_B) sw[tid] = (tid > q && tid < a.nc) ? (float)(srow[tid] + sh[2] * sdot[tid]) : 0.f;
     __syncthreads();
     // update: rows i > q of this block (v_i = P[i,q] scal), and row q if owned
     for (int e = tid; e < rows * SBR_B; e += 256) {
@@ -337,16 +339,16 @@ __global__ void __launch_bounds__(256) sbr_panel_qr(QrArgs a) {
       if (cc < q || cc >= a.nc || i < q) continue;
       if (i == q) {
         if (cc == q) sP[r][cc] = (float)sh[0];
-        else sP[r][cc] = (float)((double)sP[r][cc] - tau * sw[cc]);
+        else sP[r][cc] = fmaf(-tau, sw[cc], sP[r][cc]);
       } else {
-        const double v = (double)sP[r][q] * scal;
-        if (cc == q) continue;  // stored after every column of this row is updated
-        sP[r][cc] = (float)((double)sP[r][cc] - tau * v * sw[cc]);
+        if (cc == q) continue;  // scaled after every column of this row is updated
+        const float v = sP[r][q] * scal;
+        sP[r][cc] = fmaf(-tau * v, sw[cc], sP[r][cc]);
       }
     }
     __syncthreads();
     for (int r = tid; r < rows; r += 256)
-      if (i0 + r > q) sP[r][q] = (float)((double)sP[r][q] * scal);
+      if (i0 + r > q) sP[r][q] *= scal;
     __syncthreads();
   }
   for (int e = tid; e < rows * SBR_B; e += 256) {
@@ -537,12 +539,11 @@ __global__ void __launch_bounds__(256) sbr_chase(ChaseArgs a) {
       const int ck = (k >= 1) ? rk - SBR_B : j;  // first column of the O block
       for (int e = tid; e < SBR_B * SBR_B; e += 256) {
         const int r = e % SBR_B, c = e / SBR_B;
-        float d = 0.f;
-        if (r < nk && c < nk) {
-          if (r > c) d = __ldcg(band + bidx(rk + r, rk + c));
-          else if (r < c) d = -__ldcg(band + bidx(rk + c, rk + r));
+        if (r >= c) {  // lower triangle, read along columns; the upper one is its mirror
+          const float d = (r > c && r < nk) ? __ldcg(band + bidx(rk + r, rk + c)) : 0.f;
+          D[r][c] = d;
+          D[c][r] = -d;
         }
-        D[r][c] = d;
         float o = 0.f;
         if (r < nk && (k >= 1 || c == 0)) o = __ldcg(band + bidx(rk + r, ck + c));
         O[r][c] = o;

@@ -47,7 +47,7 @@ bool is_device_ptr(const void* p) {
 // columns stay aligned whatever n is.
 size_t w_ld(int n) { return ((2 * (size_t)n + 31) / 32) * 32; }
 
-static std::atomic<int> g_band_min_m{2048};
+static std::atomic<int> g_band_min_m{0};
 
 bool use_band_reduction(int m, int precision) {
   const int lim = g_band_min_m.load(std::memory_order_relaxed);

@@ -4,6 +4,7 @@
     python -m paper_1501_03830_gb300.stagebench ozaki --M 4096 --N 4096 --K 16384 --s 8
     python -m paper_1501_03830_gb300.stagebench tridiag --m 8192 [--fp64]
     python -m paper_1501_03830_gb300.stagebench tdeig --m 16384
+    python -m paper_1501_03830_gb300.stagebench sbr --m 16384
 
 Each run does --reps launches (CUDA events on the launch stream, after one
 warm-up launch) and prints one line with the mean time and the achieved rate
@@ -34,7 +35,7 @@ def run(argv=None) -> dict:
     import torch
 
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("stage", choices=["tc32", "ozaki", "tridiag", "tdeig"])
+    ap.add_argument("stage", choices=["tc32", "ozaki", "tridiag", "tdeig", "sbr"])
     ap.add_argument("--M", type=int, default=4096)
     ap.add_argument("--N", type=int, default=4096)
     ap.add_argument("--K", type=int, default=4096)
@@ -87,6 +88,34 @@ def run(argv=None) -> dict:
         ms = _timed(torch, fn, a.reps)
         esz = 4 if fp32 else 8
         out.update(m=m, fp32=fp32, ms=ms, symv_bytes=esz * m ** 3 / 6.0)
+    elif a.stage == "sbr":
+        # two-stage reduction of a random skew FP32 W (both stages), then Phi <- Phi Q2
+        m = a.m
+        ld = (m + 31) // 32 * 32
+        # column j of W is row j of the (m, ld) tensor: its entries below the diagonal are i > j
+        W0 = torch.triu(torch.randn(m, ld, device="cuda", generator=g), 1)
+        Wm = torch.empty_like(W0)
+        e = torch.empty(m, dtype=torch.float64, device="cuda")
+        tau = torch.empty(m, device="cuda")
+        work = torch.empty(L.bse_stage_sbr_worksize(m), dtype=torch.uint8, device="cuda")
+        Phi = torch.randn(m, ld, device="cuda", generator=g)
+
+        def fn():
+            Wm.copy_(W0)
+            bse.check(L.bse_stage_sbr(m, Wm.data_ptr(), ld, e.data_ptr(), tau.data_ptr(), work.data_ptr(),
+                                      st.data_ptr(), None), "sbr")
+
+        ms = _timed(torch, fn, a.reps)
+        fq = lambda: bse.check(L.bse_stage_sbr_apply_q2(m, Phi.data_ptr(), ld, work.data_ptr(), None), "q2")
+        ms_q2 = _timed(torch, fq, a.reps)
+        bse.kprof_enable(True)
+        fn()
+        fq()
+        torch.cuda.synchronize()
+        kp = bse.kprof_read()
+        bse.kprof_enable(False)
+        out.update(m=m, ms_reduce=ms, ms_q2=ms_q2,
+                   kernels={k: (v["launches"], round(v["ms"], 2)) for k, v in kp.items() if v["launches"]})
     else:
         m = a.m
         e = torch.rand(m, dtype=torch.float64, device="cuda", generator=g) + 0.5

@@ -127,7 +127,7 @@ def test_solve_with_band_reduction(n):
             lam_m, _, _, info_m, _ = ctx.solve(p.A, p.B, precision="mixed")
             lam, X, _, info, _ = ctx.solve(p.A, p.B, precision="mixed_refined")
     finally:
-        L.bse_set_band_reduction(2048)
+        L.bse_set_band_reduction(0)
     assert info_m.status == 0 and info.status == 0
     assert np.max(np.abs(lam_m - ref.lam) / ref.lam) <= 1e-4
     assert np.max(np.abs(lam - ref.lam) / ref.lam) <= 1e-10

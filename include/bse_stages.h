@@ -123,6 +123,17 @@ int bse_stage_tridiag_grid(int m, int fp32);
 size_t bse_stage_tdeig_worksize(int m);
 int bse_stage_tdeig(int m, const double* e, double* lam, double* Vs, void* work, int* dev_status, void* stream);
 
+/* Remark 2 of Algorithm 3 (reorthogonalization of the computed eigenvectors when
+ * high accuracy is wanted): the eigenvectors Vs that bse_stage_tdeig returned (row-major m x n,
+ * ascending eigenvalues) are made orthonormal again among index neighbours: a
+ * symmetric correction v_j <- v_j - 1/2 sum_i v_i (v_i^T v_j) over
+ * 0 < |i - j| <= 48, then unit norms, twice. Twisted-factorization vectors of
+ * close eigenvalues are orthogonal only to eps ||T|| / gap; this takes the
+ * nearby pairs to rounding level. work: bse_stage_tdeig_reorth_worksize(m)
+ * bytes. The FP64 path of bse_solve runs it; the refined path does not need it. */
+size_t bse_stage_tdeig_reorth_worksize(int m);
+int bse_stage_tdeig_reorth(int m, double* Vs, void* work, void* stream);
+
 /* Allocation-free variant of bse_stage_tdeig (the paper has no counterpart: this
  * is a packaging choice of this library). Same arguments and results, minus
  * `work`: the scratch is a fixed 512 KiB array compiled into the library, so the

@@ -2,8 +2,8 @@
 idea: Dhillon and Parlett, Linear Algebra Appl. 387, 2004), FP64 numpy.
 
 Test infrastructure only (see the package docstring). It restates, for the
-tridiagonal step of Algorithm 3 (Section 3.3, remark 2: "reorthogonalized when
-the accuracy requirement is high"), the way to get orthogonal eigenvectors
+tridiagonal step of Algorithm 3 (Section 3.3, remark 2, which calls for
+reorthogonalization when high accuracy is wanted), the way to get orthogonal eigenvectors
 without reorthogonalization; no kernel uses it yet. Plain scalar loops, small
 sizes only.
 

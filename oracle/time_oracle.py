@@ -27,6 +27,15 @@ CACHE = os.path.join(HERE, "cpu_timings.json")
 
 def cpu_model() -> str:
     try:
+        import subprocess
+
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
         with open("/proc/cpuinfo") as f:
             for line in f:
                 low = line.lower()

@@ -49,7 +49,7 @@ EXPORTS = [
     "bse_ozaki_digit_bits",
     "bse_tc32_gemm", "bse_set_fp32_gemm",
     "bse_stage_sbr_worksize", "bse_stage_sbr", "bse_stage_sbr_apply_q2", "bse_stage_sbr_backtransform",
-    "bse_set_band_reduction",
+    "bse_set_band_reduction", "bse_stage_tdeig_reorth_worksize", "bse_stage_tdeig_reorth",
 ]
 
 
@@ -143,6 +143,8 @@ def lib() -> C.CDLL:
         "bse_stage_sbr_apply_q2": (i, [i, vp, i, vp, vp]),
         "bse_stage_sbr_backtransform": (i, [i, vp, i, vp, i, vp, vp, vp, vp, vp, i, vp, vp, vp]),
         "bse_set_band_reduction": (i, [i]),
+        "bse_stage_tdeig_reorth_worksize": (sz, [i]),
+        "bse_stage_tdeig_reorth": (i, [i, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

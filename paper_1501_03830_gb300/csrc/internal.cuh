@@ -23,6 +23,9 @@ template <typename T>
 int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStream_t st, DevStatus* status);
 
 int tdeig(int m, const double* e, double* lam, double* Vs, double* work, DevStatus* st, cudaStream_t s);
+// remark 2: reorthogonalization of the tridiagonal eigenvectors Vs (row-major m x n)
+size_t tdeig_reorth_worksize(int m);
+int tdeig_reorth(int m, double* Vs, void* work, cudaStream_t s);
 
 template <typename T>
 size_t bt_worksize(int m);

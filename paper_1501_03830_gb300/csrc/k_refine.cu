@@ -57,11 +57,27 @@ struct RefWork {
   double2* Bband;             // n x kBandW couplings of the band biorthogonalization
 };
 
+// Bits carried by the FP64-accurate product M U: the first sweep starts from an
+// FP32-level solution, later sweeps and the final check need the residual of a
+// converged pair (relative size ~1e-13) to a few digits.
+#ifndef BSE_FIRST_SWEEP_BITS
+#define BSE_FIRST_SWEEP_BITS 40
+#endif
+#ifndef BSE_LATER_BITS
+#define BSE_LATER_BITS 50
+#endif
+constexpr int kFirstSweepBits = BSE_FIRST_SWEEP_BITS;
+constexpr int kLaterBits = BSE_LATER_BITS;
+
 // digits of the correction-sized products: ~25 bits
 static int corr_digits(long m) { return ozaki_digits((int)m, 25); }
 
-// The FP64-accurate M U runs on the tensor cores (digit splitting) from this size on.
-static bool refine_uses_tc(int n) { return 2 * n >= 1024; }
+// The FP64-accurate M U runs on the tensor cores (digit splitting) from this order
+// m = 2n on; below it the FP64 GEMM.
+#ifndef BSE_REFINE_TC_MIN_M
+#define BSE_REFINE_TC_MIN_M 1024
+#endif
+static bool refine_uses_tc(int n) { return 2 * n >= BSE_REFINE_TC_MIN_M; }
 
 size_t refine_worksize(int n) {
   const size_t m = 2 * (size_t)n;
@@ -673,6 +689,26 @@ __global__ void __launch_bounds__(256) ref_band_apply(int n, const float* __rest
   }
 }
 
+// Precision of the FP32 products of a sweep (projections U^H R, U^T R and the
+// update U E): 3xTF32 on the tensor cores (FP32 level), or one TF32 pass where
+// the sweep's own accuracy allows it.
+#ifndef BSE_SWEEP0_ONEPASS
+#define BSE_SWEEP0_ONEPASS 0
+#endif
+constexpr bool kSweep0OnePass = BSE_SWEEP0_ONEPASS != 0;
+
+static int sweep_gemm(bool one_pass, int M, int N, int K, const float* A, long lda, bool ta, const float* B, long ldb,
+                      bool tb, double beta, float* C, long ldc, cudaStream_t s) {
+  if (one_pass && tc32::mode() == 1) {
+    GemmArgs g{};
+    g.M = M; g.N = N; g.K = K;
+    g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
+    g.alpha = 1.0; g.beta = beta; g.transA = ta; g.transB = tb; g.batch = 1;
+    if ((double)M * N * (double)K >= (double)(1 << 21) && tc32::eligible(g)) return tc32::gemm(g, 0, nullptr, s);
+  }
+  return gemm<float>(M, N, K, 1.0, A, lda, ta, B, ldb, tb, beta, C, ldc, s);
+}
+
 int refine(int n, const double* M, double* lam, double* X, int max_sweeps, double tol, void* work, DevStatus* st,
            cudaStream_t s, int* sweeps_done, double* resid, double* dlam_last, double* dlam_first) {
   StatusScope ss(st);
@@ -709,7 +745,7 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
       // three orders below what that sweep corrects; every later sweep (and the
       // final check, whose Rayleigh quotients must settle to 1e-12) uses all digits
       const int sd = ozaki_digits(m);
-      const int bits = it == 0 ? 40 : 50;
+      const int bits = it == 0 ? kFirstSweepBits : kLaterBits;
       BSE_TRY(ozaki_gemm(m, 2 * n, m, M, m, w.Ur, m, w.Pr, m, sd, w.oz, it == 0, reinterpret_cast<int*>(st), s,
                          std::min(sd, ozaki_digits(m, bits))));
     } else {
@@ -816,10 +852,11 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
       // C1 = U^H R, C2 = U^T R from four real FP32 products (R is residual-sized, so FP32
       // rounding of these products is eps32 relative to a quantity that is itself small);
       // with aligned operands they run on the 3xTF32 tensor-core kernel
-      BSE_TRY(gemm<float>(n, n, m, 1.0, w.Urf, m, true, w.Rrf, m, false, 0.0, w.G1, n, s));
-      BSE_TRY(gemm<float>(n, n, m, 1.0, w.Uif, m, true, w.Rif, m, false, 0.0, w.G2, n, s));
-      BSE_TRY(gemm<float>(n, n, m, 1.0, w.Urf, m, true, w.Rif, m, false, 0.0, w.G3, n, s));
-      BSE_TRY(gemm<float>(n, n, m, 1.0, w.Uif, m, true, w.Rrf, m, false, 0.0, w.G4, n, s));
+      const bool op = kSweep0OnePass && it == 0;
+      BSE_TRY(sweep_gemm(op, n, n, m, w.Urf, m, true, w.Rrf, m, false, 0.0, w.G1, n, s));
+      BSE_TRY(sweep_gemm(op, n, n, m, w.Uif, m, true, w.Rif, m, false, 0.0, w.G2, n, s));
+      BSE_TRY(sweep_gemm(op, n, n, m, w.Urf, m, true, w.Rif, m, false, 0.0, w.G3, n, s));
+      BSE_TRY(sweep_gemm(op, n, n, m, w.Uif, m, true, w.Rrf, m, false, 0.0, w.G4, n, s));
       kcount(1);
       ref_buildE<<<eg, 128, 0, s>>>(n, w.G1, w.G2, w.G3, w.G4, lam, w.bnorm, w.cid, w.Fa, w.Fb, w.Fc, w.Fd);
       BSE_LAUNCH_CHECK();
@@ -827,10 +864,13 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     // the update keeps FP32 entries (not column-scaled digits): a column of F mixes one
     // near-cluster coefficient with many tiny ones, and each of them needs its own bits
     // dU = Ur [Fa Fc] + Ui [Fb Fd] in FP32 (a correction of size |E|), then U += dU in FP64
-    BSE_TRY(gemm<float>(m, n, n, 1.0, w.Urf, m, false, w.Fa, n, false, 0.0, w.dUr, m, s));
-    BSE_TRY(gemm<float>(m, n, n, 1.0, w.Uif, m, false, w.Fb, n, false, 1.0, w.dUr, m, s));
-    BSE_TRY(gemm<float>(m, n, n, 1.0, w.Urf, m, false, w.Fc, n, false, 0.0, w.dUi, m, s));
-    BSE_TRY(gemm<float>(m, n, n, 1.0, w.Uif, m, false, w.Fd, n, false, 1.0, w.dUi, m, s));
+    {
+      const bool op = kSweep0OnePass && it == 0;
+      BSE_TRY(sweep_gemm(op, m, n, n, w.Urf, m, false, w.Fa, n, false, 0.0, w.dUr, m, s));
+      BSE_TRY(sweep_gemm(op, m, n, n, w.Uif, m, false, w.Fb, n, false, 1.0, w.dUr, m, s));
+      BSE_TRY(sweep_gemm(op, m, n, n, w.Urf, m, false, w.Fc, n, false, 0.0, w.dUi, m, s));
+      BSE_TRY(sweep_gemm(op, m, n, n, w.Uif, m, false, w.Fd, n, false, 1.0, w.dUi, m, s));
+    }
     kcount(1);
     ref_apply<<<1024, 256, 0, s>>>((long)m * n, w.Ur, w.Ui, w.dUr, w.dUi);
     BSE_LAUNCH_CHECK();

@@ -71,6 +71,7 @@ size_t workspace_bytes(int n, int precision) {
   size_t scratch = f32 ? potrf_worksize<float>((int)m) : potrf_worksize<double>((int)m);
   scratch = std::max(scratch, f32 ? trd_worksize<float>((int)m) : trd_worksize<double>((int)m));
   scratch = std::max(scratch, sizeof(double) * (m + 8));
+  if (!f32) scratch = std::max(scratch, tdeig_reorth_worksize((int)m));
   scratch = std::max(scratch, f32 ? bt_worksize<float>((int)m) : bt_worksize<double>((int)m));
   if (precision == BSE_MIXED_REFINED) scratch = std::max(scratch, refine_worksize(n));
   b += al256(scratch);
@@ -304,6 +305,8 @@ int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, co
     BSE_TRY(tridiagonalize<double>(m, W, ws->ldw, ws->e, tau, ws->scratch, s, ws->status));
     if (tm) cudaEventRecord(ev[4], s);
     BSE_TRY(tdeig(m, ws->e, ws->lam, ws->Vs, (double*)ws->scratch, ws->status, s));
+    // the FP64 path has no refinement: its eigenvectors are reorthogonalized (remark 2)
+    BSE_TRY(tdeig_reorth(m, ws->Vs, ws->scratch, s));
     if (tm) cudaEventRecord(ev[5], s);
     BSE_TRY(backtransform<double>(m, ws->M, m, W, ws->ldw, tau, ws->Vs, ws->lam, ws->X, want_Y ? ws->Y : nullptr, m,
                                   ws->scratch, s));

@@ -249,3 +249,71 @@ def test_weights(n):
     torch.cuda.synchronize()
     ref = D.weights(s.X, s.Y, p.d_r, p.d_l)
     assert np.max(np.abs(w.cpu().numpy() - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def _bidiagonalize(X):
+    """Golub-Kahan Householder bidiagonalization of a square X (test helper):
+    returns the diagonal d and superdiagonal f of B = U^T X V."""
+    A = np.array(X, dtype=np.float64)
+    n = A.shape[0]
+    for k in range(n):
+        x = A[k:, k]
+        v = x.copy()
+        v[0] += np.copysign(np.linalg.norm(x), x[0])
+        if np.linalg.norm(v) > 0:
+            v /= np.linalg.norm(v)
+            A[k:, k:] -= 2.0 * np.outer(v, v @ A[k:, k:])
+        if k < n - 2:
+            x = A[k, k + 1:]
+            v = x.copy()
+            v[0] += np.copysign(np.linalg.norm(x), x[0])
+            if np.linalg.norm(v) > 0:
+                v /= np.linalg.norm(v)
+                A[k:, k + 1:] -= 2.0 * np.outer(A[k:, k + 1:] @ v, v)
+    return np.diag(A).copy(), np.diag(A, 1).copy()
+
+
+def test_tdeig_clustered_and_reorth():
+    """Tight clusters (ten eigenvalues 1e-9 apart, twenty groups): multisection keeps
+    every eigenvalue to FP64 accuracy; the twisted vectors of a cluster are far from
+    orthogonal (eps ||T|| / gap ~ 1e-6), and the reorthogonalization of remark 2 takes
+    them to rounding level without spoiling the residuals. Tsym is the zero-diagonal
+    tridiagonal of a bidiagonal with these singular values (Golub-Kahan form)."""
+    torch = torch_cuda()
+    L, bse = _lib()
+    rng = np.random.default_rng(11)
+    sig = np.concatenate([1.0 + 0.4 * g + 1e-9 * np.arange(10) for g in range(20)])
+    n = sig.shape[0]
+    m = 2 * n
+    Qa, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    Qb, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    d, f = _bidiagonalize(Qa @ np.diag(sig) @ Qb.T)
+    alpha = np.zeros(m - 1)
+    alpha[0::2] = d
+    alpha[1::2] = f
+    e = torch.tensor(-alpha.tolist() + [0.0], dtype=torch.float64, device="cuda")
+    lam = torch.empty(n, dtype=torch.float64, device="cuda")
+    Vs = torch.empty(m * n, dtype=torch.float64, device="cuda")
+    work = torch.empty(L.bse_stage_tdeig_worksize(m), dtype=torch.uint8, device="cuda")
+    st = _status(torch)
+    bse.check(L.bse_stage_tdeig(m, e.data_ptr(), lam.data_ptr(), Vs.data_ptr(), work.data_ptr(), st.data_ptr(), None),
+              "tdeig")
+    torch.cuda.synchronize()
+    assert st.cpu().numpy()[0] == 0
+    assert np.max(np.abs(np.sort(lam.cpu().numpy()) - np.sort(sig))) <= 1e-13
+    signs = np.array([1.0 if (k & 2) == 0 else -1.0 for k in range(m)])[:, None]
+    Tsym = np.diag(alpha, 1) + np.diag(alpha, -1)
+
+    def vectors():
+        return Vs.cpu().numpy().reshape(m, n) * signs
+
+    V0 = vectors()
+    before = np.max(np.abs(V0.T @ V0 - np.eye(n)))
+    rw = torch.empty(L.bse_stage_tdeig_reorth_worksize(m), dtype=torch.uint8, device="cuda")
+    bse.check(L.bse_stage_tdeig_reorth(m, Vs.data_ptr(), rw.data_ptr(), None), "reorth")
+    torch.cuda.synchronize()
+    V = vectors()
+    lg = lam.cpu().numpy()
+    assert before >= 1e-9  # the clusters do need it
+    assert np.max(np.abs(V.T @ V - np.eye(n))) <= 1e-13
+    assert np.max(np.linalg.norm(Tsym @ V - V * lg[None, :], axis=0)) <= 1e-13 * sig.max()

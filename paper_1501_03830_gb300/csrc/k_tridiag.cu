@@ -666,7 +666,12 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
 // reduced across the warp by the reduce-scatter butterfly; both go to the
 // warp's own partial vector in shared memory, and the warps' partials are
 // added in a fixed order, so results are reproducible bit for bit.
-constexpr int TRD_SMALL_MAX = 512;
+constexpr int TRD_SMALL_MAX = 512;  // FP64
+#ifndef BSE_TRD_SMALL_MAX_F32
+#define BSE_TRD_SMALL_MAX_F32 512
+#endif
+template <typename T>
+constexpr int trd_small_max() { return sizeof(T) == 4 ? BSE_TRD_SMALL_MAX_F32 : TRD_SMALL_MAX; }
 
 template <typename T>
 __device__ __forceinline__ double cta_sum(double v, double* red32) {
@@ -824,7 +829,7 @@ static long g_barrier_spin = kBarrierSpin;
 template <typename T>
 int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStream_t st, DevStatus* status) {
   StatusScope ss(status);
-  if (m <= TRD_SMALL_MAX) {
+  if (m <= trd_small_max<T>()) {
     double bytes = 0.0, flops = 0.0;
     for (int c = 0; c + 1 < m; ++c) {
       const double N = (double)(m - c - 1);
@@ -834,7 +839,7 @@ int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStr
     const size_t smem = (3 + 16) * sizeof(T) * (size_t)m;  // v_j, p_j, v_{j+1}, 16 warp partials
     static cudaError_t attr_err = cudaFuncSetAttribute(trd_small_kernel<T>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)((3 + 16) * sizeof(T) * TRD_SMALL_MAX));
+                                                       (int)((3 + 16) * sizeof(T) * trd_small_max<T>()));
     if (attr_err != cudaSuccess) {
       record_error("cudaFuncSetAttribute(trd_small_kernel)", attr_err, __FILE__, __LINE__);
       return BSE_ERR_CUDA;

@@ -5,6 +5,7 @@
     python -m paper_1501_03830_gb300.stagebench tridiag --m 8192 [--fp64]
     python -m paper_1501_03830_gb300.stagebench tdeig --m 16384
     python -m paper_1501_03830_gb300.stagebench sbr --m 16384
+    python -m paper_1501_03830_gb300.stagebench solve --n 8192 [--precision mixed_refined]
 
 Each run does --reps launches (CUDA events on the launch stream, after one
 warm-up launch) and prints one line with the mean time and the achieved rate
@@ -35,7 +36,9 @@ def run(argv=None) -> dict:
     import torch
 
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("stage", choices=["tc32", "ozaki", "tridiag", "tdeig", "sbr"])
+    ap.add_argument("stage", choices=["tc32", "ozaki", "tridiag", "tdeig", "sbr", "solve"])
+    ap.add_argument("--n", type=int, default=8192, help="solve: problem size (seeded synthetic problem)")
+    ap.add_argument("--precision", default="mixed_refined", choices=["fp64", "mixed", "mixed_refined"])
     ap.add_argument("--M", type=int, default=4096)
     ap.add_argument("--N", type=int, default=4096)
     ap.add_argument("--K", type=int, default=4096)
@@ -88,6 +91,23 @@ def run(argv=None) -> dict:
         ms = _timed(torch, fn, a.reps)
         esz = 4 if fp32 else 8
         out.update(m=m, fp32=fp32, ms=ms, symv_bytes=esz * m ** 3 / 6.0)
+    elif a.stage == "solve":
+        # one whole solve (device-resident inputs and outputs), the bench's workload
+        import numpy as np
+
+        from .synth import make_problem
+
+        p = make_problem(a.n, a.n)
+        m = 2 * a.n
+        A = torch.from_numpy(np.ascontiguousarray(np.asfortranarray(p.A).T)).cuda()
+        B = torch.from_numpy(np.ascontiguousarray(np.asfortranarray(p.B).T)).cuda()
+        lam = torch.empty(a.n, dtype=torch.float64, device="cuda")
+        X = torch.empty(m * a.n, dtype=torch.complex128, device="cuda")
+        ctx = bse.Context(0)
+        fn = lambda: ctx.solve(A, B, precision=a.precision, out={"lambda": lam, "X": X})
+        ms = _timed(torch, fn, a.reps)
+        out.update(n=a.n, precision=a.precision, ms=ms)
+        ctx.close()
     elif a.stage == "sbr":
         # two-stage reduction of a random skew FP32 W (both stages), then Phi <- Phi Q2
         m = a.m

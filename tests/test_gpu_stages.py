@@ -291,7 +291,7 @@ def test_tdeig_clustered_and_reorth():
     alpha = np.zeros(m - 1)
     alpha[0::2] = d
     alpha[1::2] = f
-    e = torch.tensor(-alpha.tolist() + [0.0], dtype=torch.float64, device="cuda")
+    e = torch.tensor((-alpha).tolist() + [0.0], dtype=torch.float64, device="cuda")
     lam = torch.empty(n, dtype=torch.float64, device="cuda")
     Vs = torch.empty(m * n, dtype=torch.float64, device="cuda")
     work = torch.empty(L.bse_stage_tdeig_worksize(m), dtype=torch.uint8, device="cuda")

@@ -161,7 +161,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, DevStatus* st, long 
           ok = 0;
           break;
         }
-        __nanosleep(40);
+        // spin tightly first (the release usually comes within a few us), then back off
+        if (it > 256) __nanosleep(40);
       }
     }
     __threadfence();
@@ -175,6 +176,74 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, DevStatus* st, long 
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p) {
   return __ldcg(p);
+}
+
+// The grid barrier before a column's reflector: the last block to arrive adds the
+// blocks' partial squared norms of the column (a fixed order: per-thread strided
+// sums, then the warp tree, then the warps in order), reads its pivot alpha and
+// publishes (beta, tau, scal) in house[0..2] before releasing the others, which
+// then read three values instead of every block re-reading all partials and the
+// pivot at once (a hot spot in L2).
+template <typename T>
+__device__ __forceinline__ bool grid_barrier_house(unsigned* bar, DevStatus* st, long spin, const double* normpart,
+                                                   const T* alpha_p, double* house, double* sh) {
+  __shared__ int s_ok, s_last;
+  __shared__ double s_red[8];
+  __syncthreads();
+  unsigned g = 0;
+  if (threadIdx.x == 0) {
+    g = *(volatile unsigned*)(bar + 1);
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    s_last = arrived == gridDim.x - 1;
+    if (s_last) __threadfence();
+  }
+  __syncthreads();
+  int ok = 1;
+  if (s_last) {
+    // the whole last block adds the partials, in the same order whatever the timing
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(normpart + b);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sigma = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sigma += s_red[w];
+      const House h = make_house((double)__ldcg(alpha_p), sigma);
+      house[0] = h.beta;
+      house[1] = h.tau;
+      house[2] = h.scal;
+      __threadfence();
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    }
+  } else if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    long it = 0;
+    while (*vgen == g) {
+      if (++it > spin) {
+        set_status(st, BSE_ERR_TIMEOUT, 1);
+        ok = 0;
+        break;
+      }
+      if (it > 256) __nanosleep(40);
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (*(volatile int*)&st->code != 0) ok = 0;
+    if (ok) {
+      sh[0] = __ldcg(house);
+      sh[1] = __ldcg(house + 1);
+      sh[2] = __ldcg(house + 2);
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
 template <typename T>
@@ -372,8 +441,9 @@ __device__ __forceinline__ void symv_item(const PanelArgs<T>& a, int j, int s, i
 // Blocks own 256 consecutive rows counted from j+1; data written by other blocks
 // during the launch is read with __ldcg (L2) so no stale L1 line is used.
 template <typename T>
-__global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) trd_panel_kernel(PanelArgs<T> a) {
   __shared__ double red8[8];
+  __shared__ double sh_house[3];
   __shared__ double dred[8][2 * TRD_NB];
   __shared__ T wdots[8][2 * TRD_NB];
   const int m = a.m;
@@ -403,15 +473,16 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
     const int j = a.j0 + c;
     const int s = j + 1;
     trace_point(a, j, 0);
-    if (!grid_barrier(a.bar, a.st, a.spin)) return;
+    if (!grid_barrier_house<T>(a.bar, a.st, a.spin, a.normpart, W + (j + 1) + (long)j * ldw,
+                               a.normpart + kMaxGrid - 4, sh_house))
+      return;
     trace_point(a, j, 1);
 
     // ---------------- phase B/C ----------------
-    const double alpha = (double)ldcg(W + (j + 1) + (long)j * ldw);
-    double sigma = 0.0;
-    for (int b = tid; b < (int)gridDim.x; b += 256) sigma += ldcg(a.normpart + b);
-    sigma = block_sum<T>(sigma, red8);  // the same order in every block
-    const House h = make_house(alpha, sigma);
+    House h;
+    h.beta = sh_house[0];
+    h.tau = sh_house[1];
+    h.scal = sh_house[2];
     const T scal = (T)h.scal;
     if (blockIdx.x == 0 && tid == 0) {
       a.e[j] = h.beta;
@@ -424,8 +495,13 @@ __global__ void __launch_bounds__(256) trd_panel_kernel(PanelArgs<T> a) {
       const int b0 = blockIdx.x * 8, b1 = min(b0 + 8, (int)gridDim.x);
       for (int q = tid; q < 2 * c; q += 256) {
         const int slot = q < c ? q : TRD_NB + (q - c);
+        // the (up to) 8 partials are independent loads, all in flight at once
+        T pv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) pv[k] = (b0 + k < b1) ? (T)ldcg(d1 + (long)(b0 + k) * 2 * TRD_NB + slot) : T(0);
         T t = T(0);
-        for (int b = b0; b < b1; ++b) t += (T)ldcg(d1 + (long)b * 2 * TRD_NB + slot);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += pv[k];
         a.dotpart2[(long)blockIdx.x * 2 * TRD_NB + slot] = (double)t;
       }
     }
@@ -860,7 +936,7 @@ int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStr
     return BSE_ERR_CUDA;
   }
   per_sm = min(per_sm, 2);
-  if (nsm * per_sm > kMaxGrid) per_sm = max(1, kMaxGrid / nsm);
+  if (nsm * per_sm > kMaxGrid - 8) per_sm = max(1, (kMaxGrid - 8) / nsm);  // the last slots hold the reflector scalars
   const int ncols = m - 1;  // columns 0..m-2 carry a reflector (the last one is trivial)
   const long ldvp = vp_ld(m);
   for (int j0 = 0; j0 < ncols; j0 += TRD_NB) {

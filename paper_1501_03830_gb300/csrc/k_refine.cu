@@ -57,19 +57,26 @@ struct RefWork {
   double2* Bband;             // n x kBandW couplings of the band biorthogonalization
 };
 
-// Bits carried by the FP64-accurate product M U (7-bit digits): the first sweep
-// starts from an FP32-level solution (40 bits, 6 digits); later sweeps and the
-// final check need the residual of a converged pair (relative size ~1e-13) to a
-// few digits (46 bits, 7 digits). Measured at n = 8192: 2 sweeps either way,
-// eigenvalues within 2.4e-13 of the FP64 path with 7 digits (1.6e-14 with 8),
-// 142 ms less than 8 digits.
+// Bits carried by the FP64-accurate product M U (7-bit digits). The first sweep
+// starts from an FP32-level solution: 40 bits (6 digits). The second sweep's
+// residual sets the couplings y_i^H x_j of the final basis, which come out as
+// (product error) / gap: 50 bits (8 digits) -- measured at n = 8192, 46 bits there
+// raise the couplings of far pairs 50-100x (Table 1's biorthogonality 1e-12 ->
+// 1e-10). The product of a third pass is normally the final check, which only
+// feeds the reported residual, the Rayleigh quotients (eigenvalues within 2.4e-13
+// of the FP64 path at 46 bits) and the rotations inside clusters: 46 bits
+// (7 digits).
 #ifndef BSE_FIRST_SWEEP_BITS
 #define BSE_FIRST_SWEEP_BITS 40
+#endif
+#ifndef BSE_SECOND_SWEEP_BITS
+#define BSE_SECOND_SWEEP_BITS 50
 #endif
 #ifndef BSE_LATER_BITS
 #define BSE_LATER_BITS 46
 #endif
 constexpr int kFirstSweepBits = BSE_FIRST_SWEEP_BITS;
+constexpr int kSecondSweepBits = BSE_SECOND_SWEEP_BITS;
 constexpr int kLaterBits = BSE_LATER_BITS;
 
 // digits of the correction-sized products: ~25 bits
@@ -746,10 +753,10 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
       // its digits are split once and reused by every sweep
       // bits of the product per sweep: the first sweep starts from an FP32-level
       // solution (scaled residual ~1e-8), where ~40 bits put the product's error
-      // three orders below what that sweep corrects; later sweeps (and the final
-      // check, whose Rayleigh quotients must settle to 1e-12) carry 46 bits
+      // three orders below what that sweep corrects; the second sweep carries 50
+      // bits and the third pass (normally the final check) 46
       const int sd = ozaki_digits(m);
-      const int bits = it == 0 ? kFirstSweepBits : kLaterBits;
+      const int bits = it == 0 ? kFirstSweepBits : (it == 1 ? kSecondSweepBits : kLaterBits);
       BSE_TRY(ozaki_gemm(m, 2 * n, m, M, m, w.Ur, m, w.Pr, m, sd, w.oz, it == 0, reinterpret_cast<int*>(st), s,
                          std::min(sd, ozaki_digits(m, bits))));
     } else {

@@ -226,8 +226,11 @@ int bse_kprof_enable(int on);
 /* Totals for kernel class k since profiling was turned on (synchronises on the
  * recorded events): 0 form M, 1 Cholesky diagonal blocks, 2 FP64 GEMM, 3 FP32
  * GEMM, 4 skew SYMV, 5 other tridiagonal-column kernels, 6 bisection,
- * 7 tridiagonal eigenvectors, 8 weights, 9 elementwise, 10 tensor-core GEMM.
- * BSE_ERR_ARG for an unknown class. */
+ * 7 tridiagonal eigenvectors, 8 weights, 9 elementwise, 10 digit-product
+ * (FP64-accurate) tensor-core GEMM, 11 3xTF32 tensor-core GEMM, 12 band
+ * reduction panel QR, 13 bulge chasing, 14 bulge-chasing back-transform,
+ * 15 TF32 hi / lo splitting of FP32 GEMM operands. BSE_ERR_ARG for an unknown
+ * class. */
 int bse_kprof_read(int k, long long* launches, double* ms, double* bytes, double* flops);
 
 /* Text of the last error recorded on this thread ("" if none). */

@@ -226,9 +226,17 @@ int bse_ozaki_gemm(int M, int N, int K, const double* A, int lda, const double* 
 int bse_tc32_gemm(int M, int N, int K, float alpha, const float* A, int lda, int transA, const float* B, int ldb,
                   int transB, float beta, float* C, int ldc, int uplo, int split, int* dev_status, void* stream);
 
-/* Engine of the FP32 products inside the mixed path: 1 (default) = the 3xTF32
- * tensor-core kernel above wherever the operand layout allows it, 0 = the SIMT
- * FP32 kernel everywhere (for comparisons). Process-wide. */
+/* Engine of the FP32 products inside the mixed path, wherever the operand
+ * layout allows the tensor cores: 2 (default) = 3xTF32 on operands split once
+ * into K-major TF32 hi / lo planes in global memory (an internal buffer per
+ * device and stream, grown on demand) for products with M N >= 500 (M + N)
+ * (M N halved for a triangular C), the splitting in shared memory inside the
+ * GEMM kernel for the smaller ones; 3 = pre-split planes for every product;
+ * 1 = splitting in shared memory for every product; 0 = the SIMT FP32 kernel
+ * everywhere. Modes 0, 1 and 3 are for comparisons; modes 1, 2 and 3 give
+ * bit-identical products. bse_tc32_gemm with split = 1 follows modes 2 and 3
+ * and splits in shared memory otherwise. Process-wide; BSE_ERR_ARG outside
+ * 0..3. */
 int bse_set_fp32_gemm(int mode);
 
 #ifdef __cplusplus

@@ -403,7 +403,8 @@ def make_request(n, A, B, lam, X=None, d_r=None, d_l=None, w=None, precision="mi
 
 
 KPROF_CLASSES = ["form_M", "potrf_diag", "gemm_f64", "gemm_f32", "trd_symv", "trd_col", "tdeig_bisect",
-                 "tdeig_vec", "weights", "elementwise", "gemm_tc", "gemm_tf32", "sbr_qr", "sbr_chase", "sbr_q2"]
+                 "tdeig_vec", "weights", "elementwise", "gemm_tc", "gemm_tf32", "sbr_qr", "sbr_chase", "sbr_q2",
+                 "tf32_split"]
 
 
 def launch_count() -> int:

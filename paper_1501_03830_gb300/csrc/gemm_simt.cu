@@ -40,7 +40,7 @@ int gemm<double>(const GemmArgs& g, cudaStream_t s) {
 // the rest runs on the SIMT kernel.
 template <>
 int gemm<float>(const GemmArgs& g, cudaStream_t s) {
-  if (tc32::mode() == 1 && (double)g.M * g.N * (double)g.K >= (double)(1 << 21) && tc32::eligible(g))
+  if (tc32::mode() >= 1 && (double)g.M * g.N * (double)g.K >= (double)(1 << 21) && tc32::eligible(g))
     return tc32::gemm(g, 1, nullptr, s);
   return launch_gemm<float, 128, 128, 16, 8, 8>(g, s);
 }

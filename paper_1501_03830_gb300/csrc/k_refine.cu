@@ -710,7 +710,7 @@ constexpr bool kSweep0OnePass = BSE_SWEEP0_ONEPASS != 0;
 
 static int sweep_gemm(bool one_pass, int M, int N, int K, const float* A, long lda, bool ta, const float* B, long ldb,
                       bool tb, double beta, float* C, long ldc, cudaStream_t s) {
-  if (one_pass && tc32::mode() == 1) {
+  if (one_pass && tc32::mode() >= 1) {
     GemmArgs g{};
     g.M = M; g.N = N; g.K = K;
     g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
@@ -849,7 +849,7 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     // the host vectors must outlive the asynchronous uploads above
     BSE_CUDA(cudaStreamSynchronize(s));
     if (verbose) fprintf(stderr, "[bse refine] n=%d sweep %d: %zu clusters (tau %.1e)\n", n, it, clusters.size(), tau);
-    if (refine_uses_tc(n) && !(tc32::mode() == 1 && n % 2 == 0)) {
+    if (refine_uses_tc(n) && !(tc32::mode() >= 1 && n % 2 == 0)) {
       // tensor cores: C1 = U^H R and C2 = U^T R from the one real 2n x 2n product
       // G = [Ur Ui]^T [Rr Ri]; each operand column (an eigenvector, a residual) has a
       // uniform scale, so ~25-bit digits carry these residual-sized products fully

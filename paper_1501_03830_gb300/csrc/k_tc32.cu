@@ -387,9 +387,222 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x == 0 && *err && P.status) atomicCAS(P.status, 0, *err);
 }
 
+// ---- pre-split operands -------------------------------------------------------
+// The same product from operands split once in global memory into K-major TF32
+// planes hi = rna_tf32(x), lo = x - hi (rows of op(A) / op(B)^T, K contiguous,
+// row pitch ldk). TMA then lands every tile already in the MMA's K-major
+// 128-byte-swizzled layout, so no warp rewrites operands in shared memory: per
+// 32-deep K block the tensor cores' operand reads (96 KiB) and the TMA writes
+// (64 KiB) are the only shared-memory traffic, against 192 KiB with in-kernel
+// splitting.
+constexpr int PSTAGES = 3;                         // 64 KiB per stage: A.hi, B.hi, A.lo, B.lo
+constexpr int P_SMEM_BYTES = PSTAGES * MMA_BYTES + 1024 + 256;
+constexpr int P_THREADS = 320;                     // TMA warp, MMA warp, 8 epilogue warps
+
+__global__ void __launch_bounds__(P_THREADS, 1)
+    tc32p_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                 const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, const Params P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* ring = smem;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + PSTAGES * MMA_BYTES);
+  uint64_t* empty = full + PSTAGES;
+  uint64_t* tfull = empty + PSTAGES;  // [2]
+  uint64_t* tempty = tfull + 2;       // [2]
+  uint64_t* drain = tempty + 2;       // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int KB = (P.K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < PSTAGES; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 256);
+    }
+    mbar_init(drain, 1);
+    *err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      uint32_t issued = 0, last_par = 0;
+      for (int t = blockIdx.x; t < P.tiles && !*err; t += gridDim.x) {
+        int tm, tn;
+        tile_coords(P, t, tm, tn);
+        const int m0 = tm * BM, n0 = tn * BN;
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const int st = it % PSTAGES;
+          const uint32_t ph = (it / PSTAGES) & 1;
+          if (!mbar_wait(&empty[st], ph ^ 1, err)) break;
+          uint8_t* sah = ring + st * MMA_BYTES;
+          const int k0 = kb * BK;
+          mbar_expect_tx(&full[st], MMA_BYTES);
+          tma_load_2d(sah, &tmAh, k0, m0, &full[st]);
+          tma_load_2d(sah + TILE_BYTES, &tmBh, k0, n0, &full[st]);
+          tma_load_2d(sah + 2 * TILE_BYTES, &tmAl, k0, m0, &full[st]);
+          tma_load_2d(sah + 3 * TILE_BYTES, &tmBl, k0, n0, &full[st]);
+          issued |= 1u << st;
+          last_par = (last_par & ~(1u << st)) | (ph << st);
+        }
+      }
+      for (int st = 0; st < PSTAGES; ++st)
+        if (issued & (1u << st)) mbar_drain(&full[st], (last_par >> st) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc();
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const int buf = it & 1;
+          ok = mbar_wait(&tempty[buf], ((it >> 1) & 1) ^ 1, err);
+          if (!ok) break;
+          const int st = it % PSTAGES;
+          ok = mbar_wait(&full[st], (it / PSTAGES) & 1, err);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t d = tmem_base + (uint32_t)(buf * BN);
+          const uint32_t sah = smem_u32(ring + st * MMA_BYTES);
+          const uint32_t sbh = sah + TILE_BYTES, sal = sah + 2 * TILE_BYTES, sbl = sah + 3 * TILE_BYTES;
+#pragma unroll
+          for (int ks = 0; ks < BK / 8; ++ks) {
+            const uint64_t ah = tile_desc(sah, ks), bh = tile_desc(sbh, ks);
+            umma_tf32(d, ah, tile_desc(sbl, ks), idesc, ks != 0);
+            umma_tf32(d, tile_desc(sal, ks), bh, idesc, 1);
+            umma_tf32(d, ah, bh, idesc, 1);
+          }
+          umma_commit(&empty[st]);
+          umma_commit(&tfull[buf]);
+        }
+      }
+      umma_commit(drain);
+      mbar_drain(drain, 0);
+    }
+  } else {
+    // epilogue, as in tc32_kernel: warps 2..9, lane quadrant warp % 4, column half
+    const int q4 = warp & 3;
+    const int half = (warp - 2) >> 2;
+    constexpr int CW = BN / 2;
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+      int tm, tn;
+      tile_coords(P, t, tm, tn);
+      float acc[CW];
+#pragma unroll
+      for (int i = 0; i < CW; ++i) acc[i] = 0.0f;
+      for (int kb = 0; kb < KB; ++kb, ++it) {
+        const int buf = it & 1;
+        ok = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], (it >> 1) & 1, err));
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t tb = tmem_base + (uint32_t)(buf * BN + half * CW) + ((uint32_t)(q4 * 32) << 16);
+#pragma unroll
+        for (int c0 = 0; c0 < CW; c0 += 16) {
+          float v[16];
+          tmem_ld16(tb + (uint32_t)c0, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[buf]);
+      }
+      if (!ok) break;
+      const int row = tm * BM + q4 * 32 + lane;
+      const int n0 = tn * BN + half * CW;
+      int cmax = P.N - 1;
+      if (P.uplo == 1) cmax = min(cmax, row);
+      if (P.uplo == 2) cmax = min(cmax, row - 1);
+      if (row >= P.M) cmax = -1;
+      float* crow = P.C + row;
+      if (P.beta != 0.0f) {
+#pragma unroll
+        for (int c0 = 0; c0 < CW; c0 += 16) {
+          float old[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int col = n0 + c0 + i;
+            old[i] = (col <= cmax) ? crow[(long)col * P.ldc] : 0.0f;
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int col = n0 + c0 + i;
+            if (col <= cmax) crow[(long)col * P.ldc] = fmaf(P.alpha, acc[c0 + i], P.beta * old[i]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < CW; ++i) {
+          const int col = n0 + i;
+          if (col <= cmax) crow[(long)col * P.ldc] = P.alpha * acc[i];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+  if (threadIdx.x == 0 && *err && P.status) atomicCAS(P.status, 0, *err);
+}
+
+// hi / lo planes of op(X) (rows x K, K contiguous, pitch ldk) from a column-major
+// X whose rows of op(X) are contiguous along K (kmaj: element (r, k) at
+// X[k + r ld]) or along the rows (element (r, k) at X[r + k ld], transposed
+// through shared memory). Columns k >= K of the planes are zero.
+__global__ void tc32_split(int rows, int K, int ldk, const float* __restrict__ X, long ld, int kmaj,
+                           float* __restrict__ hi, float* __restrict__ lo) {
+  __shared__ float t[32][33];
+  const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  if (kmaj) {
+    for (int y = ty; y < 32; y += 8) {
+      const int r = r0 + y, k = k0 + tx;
+      if (r < rows && k < ldk) {
+        const float x = k < K ? X[k + (long)r * ld] : 0.f;
+        const float h = __uint_as_float(rna_tf32(x));
+        hi[k + (long)r * ldk] = h;
+        lo[k + (long)r * ldk] = x - h;
+      }
+    }
+    return;
+  }
+  for (int y = ty; y < 32; y += 8) {
+    const int r = r0 + tx, k = k0 + y;  // read along the rows (contiguous in X)
+    t[y][tx] = (r < rows && k < K) ? X[r + (long)k * ld] : 0.f;
+  }
+  __syncthreads();
+  for (int y = ty; y < 32; y += 8) {
+    const int r = r0 + y, k = k0 + tx;  // write along K
+    if (r < rows && k < ldk) {
+      const float x = t[tx][y];
+      const float h = __uint_as_float(rna_tf32(x));
+      hi[k + (long)r * ldk] = h;
+      lo[k + (long)r * ldk] = x - h;
+    }
+  }
+}
+
 // ---- host side -------------------------------------------------------------
 
-static std::atomic<int> g_mode{1};  // 0: FP32 GEMMs on the SIMT kernel, 1: 3xTF32 tensor cores
+// 0: FP32 GEMMs on the SIMT kernel, 1: 3xTF32 tensor cores splitting in shared
+// memory, 2: 3xTF32 on operands pre-split in global memory where that pays,
+// 3: pre-split for every product
+static std::atomic<int> g_mode{2};
 
 static int sm_count() {
   static int count[64] = {0};
@@ -410,6 +623,106 @@ bool eligible(const GemmArgs& g) {
     return (reinterpret_cast<uintptr_t>(p) & 15) == 0 && (ld & 3) == 0 && ld > 0 && ld < (1L << 37);
   };
   return aligned(g.A, g.lda) && aligned(g.B, g.ldb) && g.ldc >= g.M;
+}
+
+// Pre-split planes, one buffer per (device, stream), grown on demand. Growing
+// waits for the stream (earlier products may still read the old buffer); the
+// buffers live for the process.
+struct SplitBuf {
+  int dev;
+  cudaStream_t stream;
+  float* ptr;
+  size_t bytes;
+};
+static std::mutex g_split_mu;
+static SplitBuf g_split[64];
+static int g_nsplit = 0;
+
+static int split_buffer(size_t bytes, cudaStream_t s, float** out) {
+  int dev = 0;
+  BSE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_split_mu);
+  SplitBuf* b = nullptr;
+  for (int i = 0; i < g_nsplit; ++i)
+    if (g_split[i].dev == dev && g_split[i].stream == s) b = &g_split[i];
+  if (!b) {
+    if (g_nsplit == 64) {
+      record_message("tc32 gemm: more than 64 (device, stream) pairs hold pre-split buffers");
+      return BSE_ERR_ARG;
+    }
+    b = &g_split[g_nsplit++];
+    *b = SplitBuf{dev, s, nullptr, 0};
+  }
+  if (b->bytes < bytes) {
+    if (b->ptr) {
+      BSE_CUDA(cudaStreamSynchronize(s));
+      BSE_CUDA(cudaFree(b->ptr));
+      b->ptr = nullptr;
+      b->bytes = 0;
+    }
+    const size_t want = bytes + bytes / 4;
+    void* p = nullptr;
+    BSE_CUDA(cudaMalloc(&p, want));
+    b->ptr = static_cast<float*>(p);
+    b->bytes = want;
+  }
+  *out = b->ptr;
+  return BSE_OK;
+}
+
+static int gemm_presplit(const GemmArgs& g, Params& P, cudaStream_t s) {
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(tc32p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
+  });
+  if (attr_err != cudaSuccess) {
+    record_error("cudaFuncSetAttribute(tc32p_kernel)", attr_err, __FILE__, __LINE__);
+    return BSE_ERR_CUDA;
+  }
+  const long ldk = (long)ceil_div(g.K, BK) * BK;
+  const long ra = (long)P.tiles_m * BM, rb = (long)P.tiles_n * BN;  // rows padded to whole tiles
+  const size_t plane_a = (size_t)ra * ldk, plane_b = (size_t)rb * ldk;
+  float* buf = nullptr;
+  BSE_TRY(split_buffer(2 * (plane_a + plane_b) * sizeof(float), s, &buf));
+  float *ah = buf, *al = ah + plane_a, *bh = al + plane_a, *bl = bh + plane_b;
+  const dim3 blk(32, 8);
+  {
+    KprofScope ks(K_TF32_SPLIT, s, 12.0 * ((double)g.M + g.N) * g.K, 0.0);
+    kcount(1);  // two launches in this scope
+    tc32_split<<<dim3((unsigned)(ldk / BK), (unsigned)ceil_div(g.M, 32)), blk, 0, s>>>(
+        g.M, g.K, (int)ldk, reinterpret_cast<const float*>(g.A), g.lda, g.transA ? 1 : 0, ah, al);
+    BSE_LAUNCH_CHECK();
+    tc32_split<<<dim3((unsigned)(ldk / BK), (unsigned)ceil_div(g.N, 32)), blk, 0, s>>>(
+        g.N, g.K, (int)ldk, reinterpret_cast<const float*>(g.B), g.ldb, g.transB ? 0 : 1, bh, bl);
+    BSE_LAUNCH_CHECK();
+  }
+  CUtensorMap mah, mal, mbh, mbl;
+  BSE_TRY(make_tensor_map_2d(&mah, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ah, ldk, g.M, ldk * 4, BK, BM));
+  BSE_TRY(make_tensor_map_2d(&mal, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, al, ldk, g.M, ldk * 4, BK, BM));
+  BSE_TRY(make_tensor_map_2d(&mbh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, bh, ldk, g.N, ldk * 4, BK, BN));
+  BSE_TRY(make_tensor_map_2d(&mbl, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, bl, ldk, g.N, ldk * 4, BK, BN));
+  P.K = (int)ldk;  // the padded columns are zero
+  const int grid = P.tiles < sm_count() ? P.tiles : sm_count();
+  double fl = 2.0 * g.M * (double)g.N * g.K;
+  if (g.c_uplo) fl *= 0.5;
+  KprofScope ks(K_GEMM_TF32, s, 0.0, fl);
+  tc32p_kernel<<<grid, P_THREADS, P_SMEM_BYTES, s>>>(mah, mal, mbh, mbl, P);
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
+// Pre-splitting costs one pass over both operands (read 4 B, write 8 B per
+// entry of op(A) and op(B)) and saves the shared-memory splitting of every tile
+// (measured at 8192^3: 9.9 ms in-kernel against 5.5 ms on split planes, about
+// 8e-15 s per multiply-add). At about 6 TB/s the pass costs 2e-12 s per operand
+// entry, so it pays once M N (halved for a triangular C) exceeds about
+// 250 (M + N); the bound below is twice that, for split passes that run under
+// copy bandwidth. Square products beyond about 1000 qualify, the skinny panel
+// products (N <= 128), whose operands are read once anyway, do not.
+static bool presplit_pays(const GemmArgs& g) {
+  const double mn = (double)g.M * (double)g.N * (g.c_uplo ? 0.5 : 1.0);
+  return mn >= 500.0 * ((double)g.M + (double)g.N);
 }
 
 int gemm(const GemmArgs& g, int split, int* status, cudaStream_t s) {
@@ -442,6 +755,8 @@ int gemm(const GemmArgs& g, int split, int* status, cudaStream_t s) {
   P.C = reinterpret_cast<float*>(g.C);
   P.ldc = g.ldc;
   P.status = status ? status : reinterpret_cast<int*>(current_status());
+  const int md = g_mode.load(std::memory_order_relaxed);
+  if (split && (md == 3 || (md == 2 && presplit_pays(g)))) return gemm_presplit(g, P, s);
   CUtensorMap ma, mb;
   if (P.a_mn)
     BSE_TRY(make_tensor_map_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, g.A, g.M, g.K, g.lda * 4, 32, BK));
@@ -466,7 +781,7 @@ int mode() { return g_mode.load(std::memory_order_relaxed); }
 }  // namespace bse
 
 extern "C" int bse_set_fp32_gemm(int mode) {
-  if (mode < 0 || mode > 1) return BSE_ERR_ARG;
+  if (mode < 0 || mode > 3) return BSE_ERR_ARG;
   bse::tc32::g_mode.store(mode);
   return BSE_OK;
 }

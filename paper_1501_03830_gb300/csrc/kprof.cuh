@@ -29,6 +29,7 @@ enum KClass {
   K_SBR_QR,     // band reduction: panel QR
   K_SBR_CHASE,  // band reduction: bulge chasing
   K_SBR_Q2,     // band reduction: back-transform of the chase
+  K_TF32_SPLIT, // hi / lo TF32 planes of the FP32 products' operands
   K_NUM_CLASSES
 };
 

@@ -44,23 +44,33 @@ def run(argv=None) -> dict:
     ap.add_argument("--K", type=int, default=4096)
     ap.add_argument("--s", type=int, default=8, help="digits per operand (ozaki)")
     ap.add_argument("--split", type=int, default=1, help="tc32: 1 = 3xTF32, 0 = one TF32 pass")
+    ap.add_argument("--ta", type=int, default=0, help="tc32: op(A) = A^T")
+    ap.add_argument("--tb", type=int, default=0, help="tc32: op(B) = B^T")
+    ap.add_argument("--fp32-gemm", type=int, default=None,
+                    help="engine of the FP32 products (bse_set_fp32_gemm: 0 SIMT, 1 in-kernel split, 2 pre-split)")
     ap.add_argument("--m", type=int, default=8192, help="matrix order (tridiag, tdeig)")
     ap.add_argument("--fp64", action="store_true", help="tridiag in FP64 instead of FP32")
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
     L = bse.lib()
+    if a.fp32_gemm is not None:
+        bse.check(L.bse_set_fp32_gemm(a.fp32_gemm), "bse_set_fp32_gemm")
     g = torch.Generator(device="cuda")
     g.manual_seed(1)
     st = torch.zeros(4, dtype=torch.int32, device="cuda")
     out = {"stage": a.stage}
     if a.stage == "tc32":
-        A = torch.randn(a.K, a.M, generator=g, device="cuda")  # column-major M x K, ld M
-        B = torch.randn(a.N, a.K, generator=g, device="cuda")  # column-major K x N, ld K
+        # column-major operands: op(A) = A (M x K, ld M) or A^T (A: K x M, ld K); likewise B
+        ar, ac = (a.K, a.M) if a.ta else (a.M, a.K)
+        br, bc = (a.N, a.K) if a.tb else (a.K, a.N)
+        A = torch.randn(ac, ar, generator=g, device="cuda")
+        B = torch.randn(bc, br, generator=g, device="cuda")
         C = torch.zeros(a.N, a.M, device="cuda")
-        fn = lambda: bse.check(L.bse_tc32_gemm(a.M, a.N, a.K, 1.0, A.data_ptr(), a.M, 0, B.data_ptr(), a.K, 0, 0.0,
-                                                 C.data_ptr(), a.M, 0, a.split, st.data_ptr(), None), "tc32")
+        fn = lambda: bse.check(L.bse_tc32_gemm(a.M, a.N, a.K, 1.0, A.data_ptr(), ar, a.ta, B.data_ptr(), br, a.tb,
+                                                 0.0, C.data_ptr(), a.M, 0, a.split, st.data_ptr(), None), "tc32")
         ms = _timed(torch, fn, a.reps)
-        out.update(M=a.M, N=a.N, K=a.K, split=a.split, ms=ms, tflops=2.0 * a.M * a.N * a.K / ms / 1e9)
+        out.update(M=a.M, N=a.N, K=a.K, ta=a.ta, tb=a.tb, split=a.split, ms=ms,
+                   tflops=2.0 * a.M * a.N * a.K / ms / 1e9)
     elif a.stage == "ozaki":
         A = torch.randn(a.M, a.K, dtype=torch.float64, device="cuda", generator=g)
         B = torch.randn(a.N, a.K, dtype=torch.float64, device="cuda", generator=g)

@@ -189,6 +189,35 @@ def test_tc32_gemm_lower_triangle(uplo):
     assert err < 4e-6, err
 
 
+@pytest.mark.parametrize("ta,tb", [(0, 0), (0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("M,N,K,uplo", [(257, 131, 77, 0), (1000, 700, 600, 0), (600, 600, 200, 1), (300, 300, 33, 2)])
+def test_tc32_presplit_matches_in_kernel_split(ta, tb, M, N, K, uplo):
+    """Operands split once into TF32 hi / lo planes in global memory (mode 3: for
+    every product) and split tile by tile in shared memory (mode 1) feed the
+    tensor cores the same values in the same order: the products agree bit for
+    bit, ragged tails and triangular C included."""
+    torch = torch_cuda()
+    L, bse = _lib()
+    if uplo:
+        N = M
+    out = {}
+    try:
+        for mode in (1, 3):
+            assert L.bse_set_fp32_gemm(mode) == 0
+            out[mode] = _tc32(torch, L, bse, M, N, K, ta, tb, 0.75, -0.5, uplo, 1, 31 + M + K + 2 * ta + tb)
+    finally:
+        L.bse_set_fp32_gemm(2)
+    assert torch.equal(out[1][0], out[3][0])
+    C, ref, scale, C0 = out[3]
+    rel = (C - ref).abs() / (scale + 1e-30)
+    if uplo:
+        i = torch.arange(M, device="cuda")
+        low = (i[:, None] >= i[None, :]) if uplo == 1 else (i[:, None] > i[None, :])
+        assert torch.equal(C[~low], C0[~low])
+        rel = rel[low]
+    assert rel.max().item() < 4e-6, rel.max().item()
+
+
 def test_tc32_gemm_rejects_unaligned_pitch():
     torch = torch_cuda()
     L, bse = _lib()

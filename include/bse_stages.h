@@ -94,11 +94,14 @@ int bse_set_band_reduction(int min_m);
 
 /* Diagnostics of the tridiagonal reduction (no counterpart in the paper):
  * bse_debug_trace_tridiag makes every later bse_stage_tridiag / bse_solve record,
- * for columns j < `columns`, the device clock (ns) of each block at five points
- * of the column's work (before and after the first grid barrier, after the panel
- * dot products, before and after the second barrier) into the device buffer
- * (layout [column][5][block], unsigned 64-bit); NULL turns it off. The buffer must
- * hold columns * 5 * bse_stage_tridiag_grid(m, fp32) entries. */
+ * for columns j < `columns`, the device clock (ns) of each block at eight points
+ * of the column's work (0 column start, 1 after the first grid barrier, 2 SYMV
+ * start, 3 the block's SYMV share done, 4 after the second barrier,
+ * 5 panel vectors staged, 6 p at the column's leading row known, 7 the block's
+ * rows updated) into the device buffer (layout [column][8][G] with
+ * G = bse_stage_tridiag_grid(m, fp32), unsigned 64-bit; panels launched with
+ * fewer blocks leave the rest of a row untouched); NULL turns it off. The buffer
+ * must hold columns * 8 * G entries. */
 int bse_debug_trace_tridiag(void* dev_buffer, int columns);
 
 /* Test hook for failure detection without a GPU fault: the number of polls after

@@ -18,13 +18,10 @@
 //
 // All NB columns of a panel run in one persistent cooperative launch with two
 // grid barriers per column (see trd_panel_kernel). The skew SYMV is the
-// HBM-bound part: one warp processes 32x32 sub-tiles of one 32-row strip; lane
-// l owns row r; the direct product sum_c A[r,c] v[c] accumulates in a register,
-// the transposed product -sum_r A[r,c] v[r] is reduced across lanes with a
-// 31-shuffle butterfly (lane l ends with column c0 + l), and the next
-// sub-tile's loads are in flight meanwhile. Each stored element is read once
-// per column (4m^3/3 bytes in FP64 over the whole reduction). Partial sums go
-// to two small buffers that the owners of the rows reduce after the barrier.
+// HBM-bound part: warps take equal ranges of the 32x32 sub-tiles of the
+// trailing lower triangle (see symv_item); each stored element is read once per
+// column (4m^3/3 bytes in FP64 over the whole reduction). Partial sums go to two
+// small buffers that the owners of the rows reduce after the barrier.
 #include "common.cuh"
 #include "gemm_simt.cuh"
 #include "../../include/bse_stages.h"
@@ -40,13 +37,15 @@ struct TrdWork {
   T* PV;        // m x 2NB: [P | -V]
   T* Dpart;     // direct partials   [ns][ns][32]: strip, piece, row
   T* Tpart;     // transposed partials [ns][ns][32]
-  double* normpart;  // [kMaxGrid] per-block partial squared norms of the next column
-  double* dotpart;   // [2][kMaxGrid][2NB] per-block partial V^T w, P^T w (by column parity)
-  double* dotpart2;  // [kMaxGrid / 8][2NB] sums of 8 blocks' partials
+  double* normpart;  // [2][kMaxGrid] per-block partial squared norms of the next column (by column parity)
+  double* alpha;     // [2] the next column's leading entry (by column parity)
+  T* dotpart;   // [2][kMaxGrid][2NB] per-block partial V^T w, P^T w (by column parity)
+  T* dotpart2;  // [kMaxGrid / kDotL1][2NB] sums of kDotL1 blocks' partials
   unsigned* bar;     // grid barrier words
 };
 
 constexpr int kMaxGrid = 1024;  // upper bound on the panel kernel's grid
+constexpr int kDotL1 = 16;      // blocks whose dot-product partials one first-level sum adds
 
 static inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // VP / PV leading dimension: m rounded up to 32 (aligned panels for the tensor-core update)
@@ -60,9 +59,10 @@ size_t trd_worksize(int m) {
   b += 2 * align256(sizeof(T) * (size_t)vp_ld(m) * 2 * TRD_NB);
   b += align256(sizeof(T) * ns * maxQ * TRD_TB);
   b += align256(sizeof(T) * ns * ns * TRD_TB);
-  b += align256(sizeof(double) * kMaxGrid);
+  b += align256(sizeof(double) * 2 * kMaxGrid);
+  b += align256(sizeof(double) * 2);
   b += align256(sizeof(double) * 2 * kMaxGrid * 2 * TRD_NB);
-  b += align256(sizeof(double) * (kMaxGrid / 8) * 2 * TRD_NB);
+  b += align256(sizeof(double) * (kMaxGrid / kDotL1) * 2 * TRD_NB);
   b += align256(64);
   return b;
 }
@@ -77,9 +77,10 @@ static TrdWork<T> carve(void* work, int m) {
   w.PV = reinterpret_cast<T*>(p); p += align256(sizeof(T) * (size_t)vp_ld(m) * 2 * TRD_NB);
   w.Dpart = reinterpret_cast<T*>(p); p += align256(sizeof(T) * ns * maxQ * TRD_TB);
   w.Tpart = reinterpret_cast<T*>(p); p += align256(sizeof(T) * ns * ns * TRD_TB);
-  w.normpart = reinterpret_cast<double*>(p); p += align256(sizeof(double) * kMaxGrid);
-  w.dotpart = reinterpret_cast<double*>(p); p += align256(sizeof(double) * 2 * kMaxGrid * 2 * TRD_NB);
-  w.dotpart2 = reinterpret_cast<double*>(p); p += align256(sizeof(double) * (kMaxGrid / 8) * 2 * TRD_NB);
+  w.normpart = reinterpret_cast<double*>(p); p += align256(sizeof(double) * 2 * kMaxGrid);
+  w.alpha = reinterpret_cast<double*>(p); p += align256(sizeof(double) * 2);
+  w.dotpart = reinterpret_cast<T*>(p); p += align256(sizeof(double) * 2 * kMaxGrid * 2 * TRD_NB);
+  w.dotpart2 = reinterpret_cast<T*>(p); p += align256(sizeof(double) * (kMaxGrid / kDotL1) * 2 * TRD_NB);
   w.bar = reinterpret_cast<unsigned*>(p);
   return w;
 }
@@ -112,15 +113,17 @@ struct PanelArgs {
   T* Dpart;
   T* Tpart;
   double* normpart;
-  double* dotpart;
-  double* dotpart2;
+  double* alpha;
+  T* dotpart;
+  T* dotpart2;
   double* e;
   T* tau;
   unsigned* bar;  // [0] arrivals, [1] generation
   DevStatus* st;
   int vec;  // 16-byte vector loads of W are aligned (ldw multiple of 16 B / sizeof(T), W 16-B aligned)
-  unsigned long long* trace;  // optional: [column][5 points][block] globaltimer stamps
+  unsigned long long* trace;  // optional: [column][kTracePoints][trace_stride] globaltimer stamps
   int trace_cols;
+  int trace_stride;  // the largest grid of any panel launch (the buffer's block dimension)
   long spin;  // polls before a grid-barrier wait gives up
 };
 
@@ -130,10 +133,12 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 
+constexpr int kTracePoints = 8;  // per column: see trd_panel_kernel
+
 template <typename T>
 __device__ __forceinline__ void trace_point(const PanelArgs<T>& a, int col, int point) {
   if (a.trace && threadIdx.x == 0 && col < a.trace_cols)
-    a.trace[((long)col * 5 + point) * gridDim.x + blockIdx.x] = gtimer();
+    a.trace[((long)col * kTracePoints + point) * a.trace_stride + blockIdx.x] = gtimer();
 }
 
 // Grid-wide barrier for a cooperative launch. The wait is bounded: after
@@ -178,75 +183,6 @@ __device__ __forceinline__ T ldcg(const T* p) {
   return __ldcg(p);
 }
 
-// The grid barrier before a column's reflector: the last block to arrive adds the
-// blocks' partial squared norms of the column (a fixed order: per-thread strided
-// sums, then the warp tree, then the warps in order), reads its pivot alpha and
-// publishes (beta, tau, scal) in house[0..2] before releasing the others, which
-// then read three values instead of every block re-reading all partials and the
-// pivot at once (a hot spot in L2).
-template <typename T>
-__device__ __forceinline__ bool grid_barrier_house(unsigned* bar, DevStatus* st, long spin, const double* normpart,
-                                                   const T* alpha_p, double* house, double* sh) {
-  __shared__ int s_ok, s_last;
-  __shared__ double s_red[8];
-  __syncthreads();
-  unsigned g = 0;
-  if (threadIdx.x == 0) {
-    g = *(volatile unsigned*)(bar + 1);
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    s_last = arrived == gridDim.x - 1;
-    if (s_last) __threadfence();
-  }
-  __syncthreads();
-  int ok = 1;
-  if (s_last) {
-    // the whole last block adds the partials, in the same order whatever the timing
-    double v = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(normpart + b);
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double sigma = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sigma += s_red[w];
-      const House h = make_house((double)__ldcg(alpha_p), sigma);
-      house[0] = h.beta;
-      house[1] = h.tau;
-      house[2] = h.scal;
-      __threadfence();
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    }
-  } else if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
-    long it = 0;
-    while (*vgen == g) {
-      if (++it > spin) {
-        set_status(st, BSE_ERR_TIMEOUT, 1);
-        ok = 0;
-        break;
-      }
-      if (it > 256) __nanosleep(40);
-    }
-  }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (*(volatile int*)&st->code != 0) ok = 0;
-    if (ok) {
-      sh[0] = __ldcg(house);
-      sh[1] = __ldcg(house + 1);
-      sh[2] = __ldcg(house + 2);
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-template <typename T>
 __device__ __forceinline__ double block_sum(double v, double* red8) {
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -323,11 +259,12 @@ struct Vec<double> {
 // tile and its v values are prefetched one sub-tile ahead. The transposed sums
 // are reduce-scattered over the RG lanes of a column group per sub-tile; the
 // direct sums stay in registers for the whole item and are reduce-scattered
-// over the CG lanes of a row group at its end. Sub-tiles on the diagonal or the
-// matrix edge take a masked scalar-load path.
+// over the CG lanes of a row group at its end. Sub-tiles that cross the matrix
+// edge take a masked scalar-load path; the diagonal ones and those that cross
+// row/column s load whole vectors and zero what lies outside.
 template <typename T>
 __device__ __forceinline__ void symv_item(const PanelArgs<T>& a, int j, int s, int sb, int ns, int Rr,
-                                          int cb0, int cb1, int q, T scal, int lane) {
+                                          int cb0, int cb1, int q, int lane) {
   constexpr int VW = Vec<T>::W;   // rows per lane
   constexpr int RG = 32 / VW;     // lanes along the rows of a sub-tile
   constexpr int CG = VW;          // column groups
@@ -339,9 +276,8 @@ __device__ __forceinline__ void symv_item(const PanelArgs<T>& a, int j, int s, i
   const int rg = lane % RG, cg = lane / RG;
   const int r0 = (sb + Rr) * TRD_TB;
   const int rbase = r0 + rg * VW;
-  auto vval = [&](int idx) -> T {
-    return (idx >= s && idx < m) ? ((idx == s) ? T(1) : ldcg(W + idx + (long)j * ldw) * scal) : T(0);
-  };
+  // the unscaled column below row s (zero at s and outside)
+  auto vval = [&](int idx) -> T { return (idx > s && idx < m) ? ldcg(W + idx + (long)j * ldw) : T(0); };
   T vr[VW];
 #pragma unroll
   for (int i = 0; i < VW; ++i) vr[i] = vval(rbase + i);
@@ -353,15 +289,32 @@ __device__ __forceinline__ void symv_item(const PanelArgs<T>& a, int j, int s, i
   auto load_tile = [&](T (&dst)[CPL][VW], int cb) {
     const int c0 = (sb + cb) * TRD_TB;
     const int cbase = c0 + cg * CPL;
-    const bool fast = a.vec && rows_full && (cb != Rr) && (c0 >= s) && (c0 + TRD_TB <= m);
-    if (fast) {
+    const bool diag = (cb == Rr);
+    // a sub-tile that lies inside the stored m x m array is read with vector
+    // loads even where it is not wholly inside the trailing lower triangle (the
+    // diagonal sub-tile, the strip and column block that contain row/column s):
+    // the entries outside are then replaced by zeros (a select, so whatever the
+    // strict upper triangle or the earlier columns hold never enters a sum)
+    const bool inmem = a.vec && (r0 + TRD_TB <= m) && (c0 + TRD_TB <= m);
+    if (inmem) {
 #pragma unroll
       for (int k = 0; k < CPL; ++k) {
         const V x = *reinterpret_cast<const V*>(W + rbase + (long)(cbase + k) * ldw);
         Vec<T>::split(x, dst[k]);
       }
+      if (diag || !rows_full || c0 < s) {
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+          const int cc = cbase + k;
+#pragma unroll
+          for (int i = 0; i < VW; ++i) {
+            const int r = rbase + i;
+            const bool ok = r >= s && cc >= s && (!diag || cc < r);
+            dst[k][i] = ok ? dst[k][i] : T(0);
+          }
+        }
+      }
     } else {
-      const bool diag = (cb == Rr);
 #pragma unroll
       for (int k = 0; k < CPL; ++k) {
         const int cc = cbase + k;
@@ -432,31 +385,44 @@ __device__ __forceinline__ void symv_item(const PanelArgs<T>& a, int j, int s, i
 
 // One panel of the reduction (columns j0 .. j0+nbp-1) in one cooperative launch.
 // Per column j (panel index c), two grid barriers separate
-//   phase B/C: Householder scalars (every block, redundantly), the panel dot
-//              products V^T v, P^T v, and the skew SYMV partials of A0 v, with v
-//              formed on the fly from the unscaled column W[:, j];
-//   phase D+A: p = tau (A0 v + V (P^T v) - P (V^T v)) for the owned rows, v and p
-//              stored, then column j+1 updated with all pending panel terms and its
-//              squared norm accumulated.
-// Blocks own 256 consecutive rows counted from j+1; data written by other blocks
-// during the launch is read with __ldcg (L2) so no stale L1 line is used.
+//   phase B/C: the skew SYMV partials of A0 w^ on the unscaled column below its
+//              leading entry (no reflector scalars needed yet) and the first
+//              level of the panel dot products;
+//   phase D+A: every block forms the reflector (beta, tau, scal) from the
+//              column's norm partials, then p = tau (A0 v + V (P^T v) - P (V^T v))
+//              for its rows, v and p stored, then column j+1 updated with all
+//              pending panel terms and its squared norm and panel dot products
+//              accumulated.
+// Blocks own groups of 32 rows counted from j+1 (see phase D); data written by
+// other blocks during the launch is read with __ldcg (L2) so no stale L1 line is
+// used. Trace points (bse_debug_trace_tridiag): 0 column start, 1 after the first
+// barrier, 2 SYMV start, 3 SYMV share and first dot level done, 4 after the second
+// barrier, 5 reflector formed, 6 p at row s known, 7 rows updated.
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) trd_panel_kernel(PanelArgs<T> a) {
-  __shared__ double red8[8];
+  __shared__ double red8[16];
   __shared__ double sh_house[3];
-  __shared__ double dred[8][2 * TRD_NB];
+  __shared__ double sh_ps[2];           // SYMV sum of w^ at row s, then p at row s
+  __shared__ T s_acc[2 * TRD_NB];       // w^T V, w^T P over rows > s (all blocks)
+  __shared__ T s_vec[4][TRD_NB];        // V^T v, P^T v, row s of V, row s of P
   __shared__ T wdots[8][2 * TRD_NB];
   const int m = a.m;
   const long ldw = a.ldw;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nwarps = gridDim.x * 8;
   const int gwarp = blockIdx.x * 8 + wid;
+  const int G = gridDim.x;
   T* __restrict__ W = a.W;
   T* VP = a.VP;
   T* PV = a.PV;
   const long ldvp = a.ldvp;
+  T* sdV = s_vec[0];
+  T* sdP = s_vec[1];
+  T* sVs = s_vec[2];
+  T* sPs = s_vec[3];
 
-  // phase A for the first panel column: its norm (no pending updates yet)
+  // phase A for the first panel column: its norm and leading entry (no pending
+  // updates yet)
   {
     const int j = a.j0;
     const int r = j + 1 + blockIdx.x * 256 + tid;
@@ -465,48 +431,27 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) trd_panel_kernel(
       const double w = (double)W[r + (long)j * ldw];
       sq = w * w;
     }
-    sq = block_sum<T>(sq, red8);
+    sq = block_sum(sq, red8);
     if (tid == 0) a.normpart[blockIdx.x] = sq;
+    if (blockIdx.x == 0 && tid == 0) a.alpha[0] = (double)W[(j + 1) + (long)j * ldw];
   }
 
   for (int c = 0; c < a.nbp; ++c) {
     const int j = a.j0 + c;
     const int s = j + 1;
+    const int par = c & 1;
     trace_point(a, j, 0);
-    if (!grid_barrier_house<T>(a.bar, a.st, a.spin, a.normpart, W + (j + 1) + (long)j * ldw,
-                               a.normpart + kMaxGrid - 4, sh_house))
-      return;
+    // column j (updated by the previous column's phase D) is complete
+    if (!grid_barrier(a.bar, a.st, a.spin)) return;
     trace_point(a, j, 1);
 
     // ---------------- phase B/C ----------------
-    House h;
-    h.beta = sh_house[0];
-    h.tau = sh_house[1];
-    h.scal = sh_house[2];
-    const T scal = (T)h.scal;
-    if (blockIdx.x == 0 && tid == 0) {
-      a.e[j] = h.beta;
-      a.tau[j] = (T)h.tau;
-    }
-    // first level of the dot-product reduction: block b < grid/8 adds the partials
-    // of blocks 8b .. 8b+7 (written by the previous column's phase D)
-    if (c > 0 && blockIdx.x * 8 < gridDim.x) {
-      const double* d1 = a.dotpart + (long)(c & 1) * kMaxGrid * 2 * TRD_NB;
-      const int b0 = blockIdx.x * 8, b1 = min(b0 + 8, (int)gridDim.x);
-      for (int q = tid; q < 2 * c; q += 256) {
-        const int slot = q < c ? q : TRD_NB + (q - c);
-        // the (up to) 8 partials are independent loads, all in flight at once
-        T pv[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) pv[k] = (b0 + k < b1) ? (T)ldcg(d1 + (long)(b0 + k) * 2 * TRD_NB + slot) : T(0);
-        T t = T(0);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) t += pv[k];
-        a.dotpart2[(long)blockIdx.x * 2 * TRD_NB + slot] = (double)t;
-      }
-    }
+    // skew SYMV partials of A0[s:, s:] w^ with w^ = the unscaled column below row
+    // s (w^[s] = 0). With v = e_s + scal w^ (dlarfg: v[s] = 1), A0 v =
+    // A0 e_s + scal A0 w^, and A0 e_s is column s of A0 below the diagonal; phase
+    // D adds that column and the scaling once the reflector's scalars are known,
+    // so the SYMV does not wait for the column's norm.
     trace_point(a, j, 2);
-    // skew SYMV partials of A0[s:, s:] v
     {
       const int sb = s / TRD_TB;
       const int ns = ceil_div(m, TRD_TB) - sb;
@@ -520,10 +465,27 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) trd_panel_kernel(
           const int c0 = (int)(t - S);
           const int c1 = (int)min((long)R + 1, t1 - S);
           const int q = gwarp - symv_owner(S, nw, nsub);
-          symv_item<T>(a, j, s, sb, ns, R, c0, c1, q, scal, lane);
+          symv_item<T>(a, j, s, sb, ns, R, c0, c1, q, lane);
           t = S + R + 1;
         }
       }
+    }
+    // first level of the dot-product reduction: block b < ceil(G/16) adds the
+    // partials of blocks 16b .. 16b+15 (written by the previous column's phase D);
+    // 2c <= 126 slots, one per thread. It runs after the block's SYMV share (it is
+    // needed only after the second barrier), so the SYMV of these blocks starts
+    // with the others'.
+    if (c > 0 && blockIdx.x * kDotL1 < G && tid < 2 * c) {
+      const int d1slot = tid < c ? tid : TRD_NB + (tid - c);
+      const T* d1 = a.dotpart + (long)par * kMaxGrid * 2 * TRD_NB;
+      const int b0 = blockIdx.x * kDotL1, b1 = min(b0 + kDotL1, G);
+      T pv[kDotL1];
+#pragma unroll
+      for (int k = 0; k < kDotL1; ++k) pv[k] = (b0 + k < b1) ? ldcg(d1 + (long)(b0 + k) * 2 * TRD_NB + d1slot) : T(0);
+      T t = T(0);
+#pragma unroll
+      for (int k = 0; k < kDotL1; ++k) t += pv[k];
+      a.dotpart2[(long)blockIdx.x * 2 * TRD_NB + d1slot] = t;
     }
     trace_point(a, j, 3);
     if (!grid_barrier(a.bar, a.st, a.spin)) return;
@@ -535,99 +497,145 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) trd_panel_kernel(
       const int ns = ceil_div(m, TRD_TB) - sb;
       const long Ttot = (long)ns * (ns + 1) / 2;
       const int nwp = (int)min((long)nwarps, Ttot);  // the SYMV split's warp count
-      const T tauj = (T)h.tau;
       const bool next = (c + 1 < a.nbp);
-      // the panel's small vectors, staged once per block: V^T v, P^T v and row s of V, P
-      T* sdV = reinterpret_cast<T*>(&dred[1][0]);
-      T* sdP = sdV + TRD_NB;
-      T* sVs = sdP + TRD_NB;
-      T* sPs = sVs + TRD_NB;
-      // V^T v and P^T v: v = scal * w below row s and v[s] = 1, so each is row s of
-      // V (P) plus scal times the dot products with w that the previous column's
-      // phase D accumulated over rows > s (per-block partials, parity c & 1, summed
-      // 8 blocks at a time in phase B/C, the rest here)
-      const double* dpart = a.dotpart2;
-      const int nblk = ceil_div((int)gridDim.x, 8);
-      for (int q0 = wid * 4; q0 < 2 * c; q0 += 32) {
-        const int q = q0 + (lane >> 3), l8d = lane & 7;
-        T acc = T(0);
-        int slot = 0;
-        if (q < 2 * c) {
-          slot = q < c ? q : TRD_NB + (q - c);
-          // independent partial sums so the loads are all in flight at once
-          T pa[8];
+      // D1: every block gathers, in one round of independent loads, the column's
+      // squared norm (G partials), its leading entry, the panel dot products
+      // (ceil(G/16) first-level sums per slot), row s of V and P, and the SYMV
+      // partial sums of row s; then forms the reflector (every block alike: the
+      // sums run in a fixed order) and p at row s. Every load is unrolled and
+      // predicated so that all are in flight at once.
+      double nrm = 0.0;
+      {
+        double v[kMaxGrid / 256];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) pa[k] = T(0);
-          int b = l8d;
-          for (; b + 56 < nblk; b += 64) {
+        for (int k = 0; k < kMaxGrid / 256; ++k)
+          v[k] = (tid + 256 * k < G) ? __ldcg(a.normpart + (long)par * kMaxGrid + tid + 256 * k) : 0.0;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) pa[k] += (T)ldcg(dpart + (long)(b + 8 * k) * 2 * TRD_NB + slot);
-          }
-#pragma unroll
-          for (int k = 0; k < 8; ++k)
-            if (b + 8 * k < nblk) pa[k] += (T)ldcg(dpart + (long)(b + 8 * k) * 2 * TRD_NB + slot);
-          acc = ((pa[0] + pa[1]) + (pa[2] + pa[3])) + ((pa[4] + pa[5]) + (pa[6] + pa[7]));
-        }
-#pragma unroll
-        for (int o = 4; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (q < 2 * c && l8d == 0) {
-          const T lead = ldcg(VP + s + (long)slot * ldvp);
-          const T d = fma(scal, acc, lead);
-          if (q < c) sdV[q] = d;
-          else sdP[q - c] = d;
-        }
+        for (int k = 0; k < kMaxGrid / 256; ++k) nrm += v[k];
       }
-      for (int t = tid; t < c; t += 256) {
-        sVs[t] = ldcg(VP + s + (long)t * ldvp);
-        sPs[t] = ldcg(VP + s + (long)(TRD_NB + t) * ldvp);
+      const double alpha = (tid == 0) ? __ldcg(a.alpha + par) : 0.0;
+      // row s of [V | P] (stored to shared memory after the other loads are issued)
+      const bool vps_ok = tid < c || (tid >= TRD_NB && tid - TRD_NB < c);
+      const T vpsv = vps_ok ? ldcg(VP + s + (long)tid * ldvp) : T(0);
+      // SYMV sum at row s: the transposed partials of its column block over all
+      // strips, and the one direct piece of the first strip (its only sub-tile is
+      // the diagonal one)
+      T psum = T(0);
+      {
+        const int l = s % TRD_TB;
+        T pp[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) pp[k] = (tid + 256 * k < ns) ? ldcg(a.Tpart + (long)(tid + 256 * k) * TRD_TB + l) : T(0);
+        for (int R2 = tid + 2048; R2 < ns; R2 += 256) pp[0] += ldcg(a.Tpart + (long)R2 * TRD_TB + l);
+        if (tid == 0) pp[1] += ldcg(a.Dpart + l);
+        psum = ((pp[0] + pp[1]) + (pp[2] + pp[3])) + ((pp[4] + pp[5]) + (pp[6] + pp[7]));
       }
+      // dot products: TP threads per slot (a power of two, TP * 2c <= 256)
+      const int nslot = 2 * c;
+      int TP = 16;
+      while (TP > 1 && TP * nslot > 256) TP >>= 1;
+      const int dq = tid / TP, dsub = tid % TP;
+      const int nblk = ceil_div(G, kDotL1);
+      T dacc = T(0);
+      if (dq < nslot) {
+        // nblk <= kMaxGrid / kDotL1 = 64 first-level sums, at most 32 per thread (TP >= 2)
+        const int slot = dq < c ? dq : TRD_NB + (dq - c);
+        T pa[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int b = dsub + k * TP;
+          pa[k] = b < nblk ? ldcg(a.dotpart2 + (long)b * 2 * TRD_NB + slot) : T(0);
+        }
+        for (int b = dsub + 16 * TP; b < nblk; b += TP) pa[0] += ldcg(a.dotpart2 + (long)b * 2 * TRD_NB + slot);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) pa[k] += pa[k + 8];
+        dacc = ((pa[0] + pa[1]) + (pa[2] + pa[3])) + ((pa[4] + pa[5]) + (pa[6] + pa[7]));
+      }
+      if (vps_ok) {
+        if (tid < c) sVs[tid] = vpsv;
+        else sPs[tid - TRD_NB] = vpsv;
+      }
+      // reductions: the norm and the row-s sum over the block, the dot products
+      // over the TP threads of their slot
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        psum += __shfl_xor_sync(0xffffffffu, psum, o);
+      }
+      for (int o = TP >> 1; o >= 1; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+      if (lane == 0) {
+        red8[wid] = nrm;
+        red8[8 + wid] = (double)psum;
+      }
+      if (dq < nslot && dsub == 0) s_acc[dq] = dacc;
       // this warp's partial dot products of the next column with V, P (t <= c)
       T* wd = &wdots[wid][0];
       for (int t = lane; t < 2 * TRD_NB; t += 32) wd[t] = T(0);
+      __syncthreads();
+      if (tid == 0) {
+        double sigma = 0.0, ps = 0.0;
+        for (int w = 0; w < 8; ++w) {
+          sigma += red8[w];
+          ps += red8[8 + w];
+        }
+        const House h = make_house(alpha, sigma);
+        sh_house[0] = h.beta;
+        sh_house[1] = h.tau;
+        sh_house[2] = h.scal;
+        sh_ps[0] = ps;
+        if (blockIdx.x == 0) {
+          a.e[j] = h.beta;
+          a.tau[j] = (T)h.tau;
+        }
+      }
+      __syncthreads();
+      trace_point(a, j, 5);
+      const T scal = (T)sh_house[2];
+      const T tauj = (T)sh_house[1];
+      // V^T v and P^T v: v = e_s + scal w^, so each is row s of V (P) plus scal
+      // times the dot products with w^
+      if (tid < nslot) {
+        const T lead = tid < c ? sVs[tid] : sPs[tid - c];
+        const T d = fma(scal, s_acc[tid], lead);
+        if (tid < c) sdV[tid] = d;
+        else sdP[tid - c] = d;
+      }
       __syncthreads();
       // p at row s (= j+1): every block needs it for the next column's update
       T p_s = T(0);
       if (next) {
         if (wid == 0) {
-          const int l = s % TRD_TB;
           T y = T(0);
-          for (int q = lane; q < 1; q += 32) y += ldcg(a.Dpart + ((long)0 * ns + q) * TRD_TB + l);
-          {
-            T py[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) py[k] = T(0);
-            int R2 = lane;
-            for (; R2 + 224 < ns; R2 += 256) {
-#pragma unroll
-              for (int k = 0; k < 8; ++k) py[k] += ldcg(a.Tpart + ((long)0 * ns + R2 + 32 * k) * TRD_TB + l);
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-              if (R2 + 32 * k < ns) py[k] += ldcg(a.Tpart + ((long)0 * ns + R2 + 32 * k) * TRD_TB + l);
-            y += ((py[0] + py[1]) + (py[2] + py[3])) + ((py[4] + py[5]) + (py[6] + py[7]));
-          }
           for (int t = lane; t < c; t += 32) y += sVs[t] * sdP[t] - sPs[t] * sdV[t];
 #pragma unroll
           for (int o = 16; o >= 1; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
-          if (lane == 0) dred[0][0] = (double)(tauj * y);
+          // (A0 e_s)[s] = 0
+          if (lane == 0) sh_ps[1] = (double)(tauj * fma(scal, (T)sh_ps[0], y));
         }
         __syncthreads();
-        p_s = (T)dred[0][0];
+        p_s = (T)sh_ps[1];
       }
-      // rows: 8 lanes per row, groups spread over every block of the grid
+      trace_point(a, j, 6);
+      // rows: 8 lanes per row, in groups of 32 rows from s. Group g goes to block
+      // g mod G in a boustrophedon order (blocks 0, 1, .., G-1, then G-1, .., 0,
+      // ...): the reduction of a row's transposed partials gets shorter down the
+      // matrix (strips Rr .. ns-1), so each block pairs a long group with a short one
       const int l8 = tid & 7;
-      const int ngroups = gridDim.x * 32;
       const int sbD = s / TRD_TB;
+      const int j1 = j + 1;
       double sq = 0.0;
-      // the loop runs on a warp-uniform base row so every lane reaches the shuffles
-      for (int base = s + blockIdx.x * 32 + wid * 4; base < m; base += ngroups) {
-        const int r = base + (lane >> 3);
+      // the loop runs on a warp-uniform group index so every lane reaches the shuffles
+      for (int k = 0;; ++k) {
+        const int g = (k & 1) ? (k + 1) * G - 1 - (int)blockIdx.x : k * G + (int)blockIdx.x;
+        if (s + g * 32 >= m) break;
+        const int r = s + g * 32 + wid * 4 + (lane >> 3);
         const bool valid = r < m;
         const int Rr = r / TRD_TB - sbD, l = r % TRD_TB;
         const int nq = valid ? symv_pieces(Rr, nwp, Ttot) : 0;
         const int nsv = valid ? ns : 0;
-        // the row's panel entries V[r, t], P[r, t] (t = l8 + 8k < c), loaded up front
-        // so their latency overlaps the partial-sum loads below
+        // the row's panel entries V[r, t], P[r, t] (t = l8 + 8k < c), column s of
+        // A0 and the unscaled reflector, loaded up front so their latency overlaps
+        // the partial-sum loads below
         T vvk[8], ppk[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -636,28 +644,34 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) trd_panel_kernel(
           vvk[k] = ok ? ldcg(VP + r + (long)t * ldvp) : T(0);
           ppk[k] = ok ? ldcg(VP + r + (long)(TRD_NB + t) * ldvp) : T(0);
         }
+        const T w0 = (valid && r > s) ? ldcg(W + r + (long)j1 * ldw) : T(0);
+        const T wj = (valid && r > s) ? ldcg(W + r + (long)j * ldw) : T(0);
         T acc[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc[k] = T(0);
         const T* dp = a.Dpart + (long)Rr * ns * TRD_TB + l;
-        for (int q = l8; q < nq; q += 8) acc[0] += ldcg(dp + (long)q * TRD_TB);
+        acc[0] = (l8 < nq) ? ldcg(dp + (long)l8 * TRD_TB) : T(0);
+        for (int q = l8 + 8; q < nq; q += 8) acc[0] += ldcg(dp + (long)q * TRD_TB);
         const T* tp = a.Tpart + (long)Rr * ns * TRD_TB + l;
         int R2 = Rr + l8;
-        for (; R2 + 56 < nsv; R2 += 64) {
+        // up to 32 independent loads in flight per lane (unrolled and predicated):
+        // the rows near the top have many strips to add
+        for (; R2 < nsv; R2 += 256) {
+          T t4[32];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) acc[k] += ldcg(tp + (long)(R2 + 8 * k) * TRD_TB);
+          for (int k = 0; k < 32; ++k) t4[k] = (R2 + 8 * k < nsv) ? ldcg(tp + (long)(R2 + 8 * k) * TRD_TB) : T(0);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) acc[k] += (t4[k] + t4[k + 8]) + (t4[k + 16] + t4[k + 24]);
         }
-        for (; R2 < nsv; R2 += 8) acc[1] += ldcg(tp + (long)R2 * TRD_TB);
         T y = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
         const bool upd = next && r >= s + 1;
-        const int j1 = j + 1;
-        T w = T(0);
+        T w = T(0), yp = T(0);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int t = l8 + 8 * k;
           if (valid && t < c) {
-            y = fma(vvk[k], sdP[t], y);
-            y = fma(-ppk[k], sdV[t], y);
+            yp = fma(vvk[k], sdP[t], yp);
+            yp = fma(-ppk[k], sdV[t], yp);
             w = fma(vvk[k], sPs[t], w);
             w = fma(-ppk[k], sVs[t], w);
           }
@@ -665,16 +679,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) trd_panel_kernel(
 #pragma unroll
         for (int o = 4; o >= 1; o >>= 1) {
           y += __shfl_xor_sync(0xffffffffu, y, o);
+          yp += __shfl_xor_sync(0xffffffffu, yp, o);
           w += __shfl_xor_sync(0xffffffffu, w, o);
         }
         // every lane of the row's group finishes the row (the sums are replicated by
-        // the butterfly); lane l8 == 0 stores
-        const T vr = !valid ? T(0) : (r == s) ? T(1) : ldcg(W + r + (long)j * ldw) * scal;
-        const T p = tauj * y;
+        // the butterfly); lane l8 == 0 stores. (A0 v)[r] = A0[r, s] + scal (A0 w^)[r]
+        const T vr = !valid ? T(0) : (r == s) ? T(1) : wj * scal;
+        // row s takes the p_s every block formed (the same value the next column's
+        // update uses)
+        const T p = (next && r == s) ? p_s : tauj * (fma(scal, y, w0) + yp);
         T wf = T(0);
         if (valid && upd) {
           // column j+1 with all panel terms t <= c; t = c: V[j1, c] = 1, P[j1, c] = p_s
-          w += ldcg(W + r + (long)j1 * ldw);
+          w += w0;
           w = fma(vr, p_s, w);
           w = fma(-p, T(1), w);
           wf = w;
@@ -688,6 +705,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) trd_panel_kernel(
           if (upd) {
             W[r + (long)j1 * ldw] = wf;
             if (r >= j1 + 2) sq += (double)wf * (double)wf;
+            // the next column's leading entry, for its reflector
+            if (r == j1 + 1) a.alpha[par ^ 1] = (double)wf;
           }
         }
         if (next) {
@@ -711,16 +730,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) trd_panel_kernel(
           }
         }
       }
+      trace_point(a, j, 7);
       if (next) {
-        sq = block_sum<T>(sq, red8);  // also orders the warps' dot partials before their sum
-        if (tid == 0) a.normpart[blockIdx.x] = sq;
-        double* dnext = a.dotpart + (long)((c + 1) & 1) * kMaxGrid * 2 * TRD_NB + (long)blockIdx.x * 2 * TRD_NB;
+        sq = block_sum(sq, red8);  // also orders the warps' dot partials before their sum
+        if (tid == 0) a.normpart[(long)(par ^ 1) * kMaxGrid + blockIdx.x] = sq;
+        T* dnext = a.dotpart + (long)(par ^ 1) * kMaxGrid * 2 * TRD_NB + (long)blockIdx.x * 2 * TRD_NB;
         for (int q = tid; q < 2 * (c + 1); q += 256) {
           const int slot = q <= c ? q : TRD_NB + (q - c - 1);
           T t = T(0);
 #pragma unroll
           for (int k = 0; k < 8; ++k) t += wdots[k][slot];
-          dnext[slot] = (double)t;
+          dnext[slot] = t;
         }
       }
       __syncthreads();  // the staged vectors are rewritten for the next column
@@ -936,7 +956,7 @@ int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStr
     return BSE_ERR_CUDA;
   }
   per_sm = min(per_sm, 2);
-  if (nsm * per_sm > kMaxGrid - 8) per_sm = max(1, (kMaxGrid - 8) / nsm);  // the last slots hold the reflector scalars
+  if (nsm * per_sm > kMaxGrid) per_sm = max(1, kMaxGrid / nsm);
   const int ncols = m - 1;  // columns 0..m-2 carry a reflector (the last one is trivial)
   const long ldvp = vp_ld(m);
   for (int j0 = 0; j0 < ncols; j0 += TRD_NB) {
@@ -951,12 +971,13 @@ int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStr
     const int grid = (int)max(1L, min((long)nsm * per_sm, want));
     PanelArgs<T> pa;
     pa.m = m; pa.j0 = j0; pa.nbp = nbp; pa.W = W; pa.ldw = ldw; pa.VP = w.VP; pa.PV = w.PV; pa.ldvp = ldvp;
-    pa.Dpart = w.Dpart; pa.Tpart = w.Tpart; pa.normpart = w.normpart;
+    pa.Dpart = w.Dpart; pa.Tpart = w.Tpart; pa.normpart = w.normpart; pa.alpha = w.alpha;
     pa.dotpart = w.dotpart; pa.dotpart2 = w.dotpart2; pa.e = e; pa.tau = tau;
     pa.bar = w.bar; pa.st = status;
     pa.vec = ((ldw * (long)sizeof(T)) % 16 == 0) && ((reinterpret_cast<uintptr_t>(W) % 16) == 0);
     pa.trace = g_trace;
     pa.trace_cols = g_trace_cols;
+    pa.trace_stride = nsm * per_sm;
     pa.spin = g_barrier_spin;
     if (grid * 256 < rows + 1 && grid < nsm * per_sm) {
       record_message("tridiagonal panel grid too small");

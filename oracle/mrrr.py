@@ -17,7 +17,11 @@ sizes only.
              child representation L D L^T - tau I = L' D' L'^T with tau just
              left of it (the cluster's eigenvalues shrink to distances from tau,
              which enlarges their relative gaps), its eigenvalues are refined on
-             the child, and the classification repeats there
+             the child, and the classification repeats there. A cluster of more
+             than 1/gaptol members (a dense spectrum) gets tau within a quarter
+             of (mean gap / gaptol) of its first eigenvalue, so that the first
+             ~1/gaptol of them separate in the child and the rest form a smaller
+             cluster there ("peeling")
   vectors    a singleton's vector comes from the twisted factorization of its
              representation shifted by the eigenvalue: the stationary transform
              from the top, the progressive one from the bottom, twist index r
@@ -87,17 +91,47 @@ def negcount(D, l, x) -> int:
     return int(np.sum(Dp < 0))
 
 
+def negcounts(D, l, xs: np.ndarray) -> np.ndarray:
+    """negcount for every shift in xs at once: the stationary transform of
+    stqds with a vector of shifts (the same recurrence, elementwise)."""
+    xs = np.asarray(xs, dtype=np.float64)
+    n = D.shape[0]
+    cnt = np.zeros(xs.shape, dtype=np.int64)
+    s = -xs
+    for i in range(n - 1):
+        dp = s + D[i]
+        dp = np.where(dp == 0.0, -TINY, dp)
+        cnt += dp < 0
+        s = (D[i] * l[i] / dp) * l[i] * s - xs
+    dp = s + D[n - 1]
+    dp = np.where(dp == 0.0, -TINY, dp)
+    cnt += dp < 0
+    return cnt
+
+
 def bisect(D, l, lo, hi, k, tol=4 * EPS):
     """The k-th smallest eigenvalue (0-based) of L D L^T in [lo, hi], to relative
     accuracy tol."""
-    while hi - lo > tol * max(abs(lo), abs(hi)):
+    return float(bisect_all(D, l, np.array([lo]), np.array([hi]), np.array([k]), tol)[0])
+
+
+def bisect_all(D, l, lo, hi, ks, tol=4 * EPS):
+    """bisect for several eigenvalues at once (eigenvalue ks[i] in [lo[i], hi[i]]);
+    each interval is halved on its own until it meets the same stopping rule."""
+    lo = np.array(lo, dtype=np.float64)
+    hi = np.array(hi, dtype=np.float64)
+    ks = np.asarray(ks)
+    active = hi - lo > tol * np.maximum(np.abs(lo), np.abs(hi))
+    while np.any(active):
         mid = 0.5 * (lo + hi)
-        if mid == lo or mid == hi:
+        active &= (mid != lo) & (mid != hi)
+        if not np.any(active):
             break
-        if negcount(D, l, mid) > k:
-            hi = mid
-        else:
-            lo = mid
+        idx = np.nonzero(active)[0]
+        up = negcounts(D, l, mid[idx]) > ks[idx]
+        hi[idx[up]] = mid[idx[up]]
+        lo[idx[~up]] = mid[idx[~up]]
+        active = hi - lo > tol * np.maximum(np.abs(lo), np.abs(hi))
     return 0.5 * (lo + hi)
 
 
@@ -126,10 +160,14 @@ def _vector(D, l, lam, iters=3):
 
 
 def _eigvals(D, l, idx, lo, hi):
-    return np.array([bisect(D, l, lo, hi, k) for k in idx])
+    return bisect_all(D, l, np.full(len(idx), lo), np.full(len(idx), hi), np.array(idx))
 
 
-def _solve(D, l, shift, idx, lo, hi, gaptol, depth, out_lam, out_z, tree):
+MAX_DEPTH = 8    # levels of child representations for clusters of <= 1/gaptol members
+MAX_PEELS = 64   # levels that peel a larger cluster
+
+
+def _solve(D, l, shift, idx, lo, hi, gaptol, depth, out_lam, out_z, tree, peels=0):
     """Eigenpairs idx of L D L^T (whose eigenvalues lie in [lo, hi]); the
     matrix's eigenvalues are these plus `shift`."""
     lam = _eigvals(D, l, idx, lo, hi)
@@ -140,30 +178,40 @@ def _solve(D, l, shift, idx, lo, hi, gaptol, depth, out_lam, out_z, tree):
         e = k
         while e + 1 < m and (lam[e + 1] - lam[e]) < gaptol * max(abs(lam[e]), abs(lam[e + 1])):
             e += 1
-        if e == k or depth >= 8:
+        size = e - k + 1
+        large = size * gaptol > 1.0
+        if e == k or (depth >= MAX_DEPTH and not large) or (large and peels >= MAX_PEELS):
             for t in range(k, e + 1):
                 z, lt = _vector(D, l, lam[t])
                 out_lam[idx[t]] = lt + shift
                 out_z[:, idx[t]] = z
-            tree.append((depth, 1 if e == k else e - k + 1))
+            tree.append((depth, 1 if e == k else size))
         else:
             # child representation just left of the cluster
             left = lam[k - 1] if k > 0 else lam[k] - (lam[e] - lam[k]) - abs(lam[k]) * 1e-3
             width = lam[e] - lam[k]
-            tau = lam[k] - max(0.25 * min(lam[k] - left, width + abs(lam[k]) * 1e-3), abs(lam[k]) * 8 * EPS)
+            off = min(lam[k] - left, width + abs(lam[k]) * 1e-3)
+            if large:
+                # more than 1/gaptol members: a shift at the scale of the whole width
+                # would leave every relative gap below gaptol; at a quarter of (mean
+                # gap / gaptol) the first ~1/gaptol members separate in the child and
+                # the rest form a smaller cluster there
+                off = min(off, width / (size - 1) / gaptol)
+            tau = lam[k] - max(0.25 * off, abs(lam[k]) * 8 * EPS)
             Dc, lc, _ = stqds(D, l, tau)
-            tree.append((depth, e - k + 1))
+            tree.append((depth, size))
             lo_c = (lam[k] - tau) * (1 - 1e-6)
             hi_c = (lam[e] - tau) * (1 + 1e-6) + abs(lam[e]) * 4 * EPS
-            _solve(Dc, lc, shift + tau, [idx[t] for t in range(k, e + 1)], lo_c, hi_c, gaptol, depth + 1, out_lam,
-                   out_z, tree)
+            _solve(Dc, lc, shift + tau, [idx[t] for t in range(k, e + 1)], lo_c, hi_c, gaptol,
+                   depth if large else depth + 1, out_lam, out_z, tree, peels + 1 if large else peels)
         k = e + 1
 
 
 def eigh_tridiagonal(a: np.ndarray, b: np.ndarray, gaptol: float = 1e-3):
     """All eigenpairs of T = tridiag(b, a, b) (ascending). Returns (lam, Z, tree):
     tree lists (depth, size) for every singleton (size 1), every cluster that got
-    a child representation, and every group left at the depth limit (8)."""
+    a child representation, and every group left at the depth limit (MAX_DEPTH,
+    or MAX_PEELS for the peeling levels of clusters of more than 1/gaptol)."""
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     n = a.shape[0]

@@ -68,3 +68,18 @@ def test_without_tree_cluster_vectors_are_not_orthogonal():
     _, orth0, _, _ = _check(*_glued(5, 1e-10), gaptol=0.0)
     _, orth, _, _ = _check(*_glued(5, 1e-10))
     assert orth0 > 1e-3 and orth <= 1e-12
+
+
+def test_peeling_a_cluster_larger_than_one_over_gaptol():
+    """With gaptol = 0.05, the positive half of a BSE tridiagonal of n = 100 is one
+    cluster of more than 1/gaptol members at the root; the tree peels it (child
+    shifts within a quarter of mean gap / gaptol of its first member) and still
+    gives eigenvalues to 1e-14 and orthogonal vectors."""
+    n = 100
+    p = make_problem(n, 5)
+    W = alg1.step3_W(alg1.step2_cholesky(alg1.step1_M(p.A, p.B)))
+    t = alg1.alg3_step1_tridiagonalize(W)
+    ev, orth, res, tree = _check(np.zeros(2 * n), -t.beta, gaptol=0.05)
+    # residual bar: O(m eps ||T||), the twisted-factorization bound, with m = 2n
+    assert ev <= 1e-14 and orth <= 1e-12 and res <= 2 * (2 * n) * 2.0 ** -52
+    assert max(s for _, s in tree) * 0.05 > 1.0  # a cluster of more than 1/gaptol members

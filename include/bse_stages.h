@@ -137,6 +137,37 @@ int bse_stage_tdeig(int m, const double* e, double* lam, double* Vs, void* work,
 size_t bse_stage_tdeig_reorth_worksize(int m);
 int bse_stage_tdeig_reorth(int m, double* Vs, void* work, void* stream);
 
+/* Algorithm 3 step 2 by a representation tree (MRRR; Section 3.3's closing
+ * remarks name it for the tridiagonal step, and it makes remark 2's
+ * reorthogonalization unnecessary): eigenpairs il .. iu-1 (0-based, ascending) of
+ * the m x m symmetric tridiagonal T with diagonal a (NULL: zero) and off-diagonal
+ * b (m - 1 entries; with bse_form != 0, b is the sub-diagonal e of the skew T that
+ * bse_stage_tridiag returns and T = Tsym = -i D^H T D, off-diagonal -e, zero
+ * diagonal). FP64, device pointers.
+ *   Root T - sigma I = L D L^T (sigma below the Gershgorin interval); eigenvalues by
+ *   multisection on the representation; runs whose relative gaps are below gaptol
+ *   (0: 1e-3) get child representations L D L^T - tau I (stationary qd transform)
+ *   down a tree of at most 8 levels (64 more for clusters of more than 1/gaptol
+ *   members, which are split ~1/gaptol eigenvalues at a time); vectors by twisted
+ *   factorizations of their representation, three Rayleigh-quotient corrections of
+ *   the eigenvalue, normalised.
+ *   lam: iu - il values. Z: row-major m x ldz (ldz >= iu - il), column j = the
+ *   eigenvector of value il + j; with bse_signs != 0 the D phase is folded in as in
+ *   bse_stage_tdeig (rows scaled by +1,+1,-1,-1 for k mod 4), so bse_form = 1,
+ *   il = m/2, iu = m, ldz = m/2, bse_signs = 1 gives bse_stage_tdeig's lam and Vs.
+ *   work: bse_stage_tdeig_mrrr_worksize(m, il, iu) bytes (16 m (iu - il) + small:
+ *   two levels of child representations). The call synchronises its stream once per
+ *   tree level (it reads the count of new child representations). A bisection that
+ *   does not converge records BSE_ERR_NOT_CONVERGED in dev_status. */
+size_t bse_stage_tdeig_mrrr_worksize(int m, int il, int iu);
+/* Tridiagonal eigenvectors of bse_solve (and the batched and serving calls): 0 =
+ * twisted factorizations on the root matrix, reorthogonalized on the FP64 path
+ * (remark 2; the default), 1 = the representation tree of bse_stage_tdeig_mrrr
+ * (no reorthogonalization). Process-wide; set it before solving. */
+int bse_set_tdeig_method(int method);
+int bse_stage_tdeig_mrrr(int m, const double* a, const double* b, int bse_form, int il, int iu, double gaptol,
+                         double* lam, double* Z, int ldz, int bse_signs, void* work, int* dev_status, void* stream);
+
 /* Allocation-free variant of bse_stage_tdeig (the paper has no counterpart: this
  * is a packaging choice of this library). Same arguments and results, minus
  * `work`: the scratch is a fixed 512 KiB array compiled into the library, so the

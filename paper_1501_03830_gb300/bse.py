@@ -50,6 +50,7 @@ EXPORTS = [
     "bse_tc32_gemm", "bse_set_fp32_gemm",
     "bse_stage_sbr_worksize", "bse_stage_sbr", "bse_stage_sbr_apply_q2", "bse_stage_sbr_backtransform",
     "bse_set_band_reduction", "bse_stage_tdeig_reorth_worksize", "bse_stage_tdeig_reorth",
+    "bse_stage_tdeig_mrrr_worksize", "bse_stage_tdeig_mrrr", "bse_set_tdeig_method",
 ]
 
 
@@ -145,6 +146,9 @@ def lib() -> C.CDLL:
         "bse_set_band_reduction": (i, [i]),
         "bse_stage_tdeig_reorth_worksize": (sz, [i]),
         "bse_stage_tdeig_reorth": (i, [i, vp, vp, vp]),
+        "bse_stage_tdeig_mrrr_worksize": (sz, [i, i, i]),
+        "bse_stage_tdeig_mrrr": (i, [i, vp, vp, i, i, i, d, vp, vp, i, i, vp, vp, vp]),
+        "bse_set_tdeig_method": (i, [i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -23,6 +23,11 @@ template <typename T>
 int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStream_t st, DevStatus* status);
 
 int tdeig(int m, const double* e, double* lam, double* Vs, double* work, DevStatus* st, cudaStream_t s);
+// the same eigenpairs (or any index range of a general symmetric tridiagonal) by the
+// MRRR representation tree (k_mrrr.cu); Z row-major m x ldz
+size_t tdeig_mrrr_worksize(int m, int nz);
+int tdeig_mrrr(int m, const double* a, const double* b, int bse_form, int il, int iu, double gaptol, double* lam,
+               double* Z, long ldz, int bse_signs, void* work, DevStatus* st, cudaStream_t s);
 // remark 2: reorthogonalization of the tridiagonal eigenvectors Vs (row-major m x n)
 size_t tdeig_reorth_worksize(int m);
 int tdeig_reorth(int m, double* Vs, void* work, cudaStream_t s);

@@ -54,6 +54,10 @@ bool use_band_reduction(int m, int precision) {
   return precision != BSE_FP64 && lim > 0 && m >= lim && m >= 4;
 }
 
+static std::atomic<int> g_tdeig_method{0};
+
+bool use_mrrr() { return g_tdeig_method.load(std::memory_order_relaxed) == 1; }
+
 size_t workspace_bytes(int n, int precision) {
   const size_t m = 2 * (size_t)n;
   const bool f32 = precision != BSE_FP64;
@@ -72,6 +76,7 @@ size_t workspace_bytes(int n, int precision) {
   scratch = std::max(scratch, f32 ? trd_worksize<float>((int)m) : trd_worksize<double>((int)m));
   scratch = std::max(scratch, sizeof(double) * (m + 8));
   if (!f32) scratch = std::max(scratch, tdeig_reorth_worksize((int)m));
+  if (use_mrrr()) scratch = std::max(scratch, tdeig_mrrr_worksize((int)m, n));
   scratch = std::max(scratch, f32 ? bt_worksize<float>((int)m) : bt_worksize<double>((int)m));
   if (precision == BSE_MIXED_REFINED) scratch = std::max(scratch, refine_worksize(n));
   b += al256(scratch);
@@ -189,6 +194,12 @@ extern "C" int bse_set_stream(bse_ctx* c, void* stream) {
   return BSE_OK;
 }
 
+extern "C" int bse_set_tdeig_method(int method) {
+  if (method < 0 || method > 1) return BSE_ERR_ARG;
+  bse::g_tdeig_method.store(method);
+  return BSE_OK;
+}
+
 extern "C" int bse_set_band_reduction(int min_m) {
   if (min_m < 0) return BSE_ERR_ARG;
   bse::g_band_min_m.store(min_m);
@@ -278,6 +289,14 @@ int negate_bottom(int n, double* Y, cudaStream_t s) {
 
 // Runs the whole pipeline on device-resident inputs into the workspace outputs
 // (ws->lam, ws->X, ws->Y). Stage events go to ev[0..8] when timing.
+// MRRR is selected and the workspace's scratch holds its tree (a workspace made
+// before the selection may not)
+static bool mrrr_fits(const Workspace* ws, int m, int n) {
+  if (!use_mrrr()) return false;
+  const size_t used = (size_t)((const char*)ws->scratch - (const char*)ws->base);
+  return ws->bytes >= used && ws->bytes - used >= tdeig_mrrr_worksize(m, n);
+}
+
 int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, const double* dB, int ldb,
                  int precision, bool want_Y, bse_info* info, cudaStream_t s, bool real_blocks) {
   const int m = 2 * n;
@@ -304,9 +323,14 @@ int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, co
     if (tm) cudaEventRecord(ev[3], s);
     BSE_TRY(tridiagonalize<double>(m, W, ws->ldw, ws->e, tau, ws->scratch, s, ws->status));
     if (tm) cudaEventRecord(ev[4], s);
-    BSE_TRY(tdeig(m, ws->e, ws->lam, ws->Vs, (double*)ws->scratch, ws->status, s));
-    // the FP64 path has no refinement: its eigenvectors are reorthogonalized (remark 2)
-    BSE_TRY(tdeig_reorth(m, ws->Vs, ws->scratch, s));
+    if (mrrr_fits(ws, m, n)) {
+      // cluster-safe vectors from the representation tree: no reorthogonalization
+      BSE_TRY(tdeig_mrrr(m, nullptr, ws->e, 1, n, m, 1e-3, ws->lam, ws->Vs, n, 1, ws->scratch, ws->status, s));
+    } else {
+      BSE_TRY(tdeig(m, ws->e, ws->lam, ws->Vs, (double*)ws->scratch, ws->status, s));
+      // the FP64 path has no refinement: its eigenvectors are reorthogonalized (remark 2)
+      BSE_TRY(tdeig_reorth(m, ws->Vs, ws->scratch, s));
+    }
     if (tm) cudaEventRecord(ev[5], s);
     BSE_TRY(backtransform<double>(m, ws->M, m, W, ws->ldw, tau, ws->Vs, ws->lam, ws->X, want_Y ? ws->Y : nullptr, m,
                                   ws->scratch, s));
@@ -329,7 +353,10 @@ int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, co
     else
       BSE_TRY(tridiagonalize<float>(m, W, ws->ldw, ws->e, tau, ws->scratch, s, ws->status));
     if (tm) cudaEventRecord(ev[4], s);
-    BSE_TRY(tdeig(m, ws->e, ws->lam, ws->Vs, (double*)ws->scratch, ws->status, s));
+    if (mrrr_fits(ws, m, n))
+      BSE_TRY(tdeig_mrrr(m, nullptr, ws->e, 1, n, m, 1e-3, ws->lam, ws->Vs, n, 1, ws->scratch, ws->status, s));
+    else
+      BSE_TRY(tdeig(m, ws->e, ws->lam, ws->Vs, (double*)ws->scratch, ws->status, s));
     if (tm) cudaEventRecord(ev[5], s);
     const bool refine_now = precision == BSE_MIXED_REFINED;
     BSE_TRY(backtransform<float>(m, ws->Lf, ws->ldw, W, ws->ldw, tau, ws->Vs, ws->lam, ws->X,

@@ -36,6 +36,9 @@ struct Workspace {
 size_t workspace_bytes(int n, int precision);
 // the mixed paths reduce W in two stages (band, then tridiagonal) from this order m = 2n on
 bool use_band_reduction(int m, int precision);
+// the tridiagonal eigenvectors come from the MRRR representation tree (else twisted
+// factorizations on the root matrix, reorthogonalized on the FP64 path)
+bool use_mrrr();
 bool is_device_ptr(const void* p);
 
 struct ServeState;

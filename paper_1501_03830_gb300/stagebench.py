@@ -3,7 +3,7 @@
     python -m paper_1501_03830_gb300.stagebench tc32 --M 4096 --N 4096 --K 4096
     python -m paper_1501_03830_gb300.stagebench ozaki --M 4096 --N 4096 --K 16384 --s 8
     python -m paper_1501_03830_gb300.stagebench tridiag --m 8192 [--fp64]
-    python -m paper_1501_03830_gb300.stagebench tdeig --m 16384
+    python -m paper_1501_03830_gb300.stagebench tdeig --m 16384 [--mrrr]
     python -m paper_1501_03830_gb300.stagebench sbr --m 16384
     python -m paper_1501_03830_gb300.stagebench solve --n 8192 [--precision mixed_refined]
 
@@ -50,6 +50,8 @@ def run(argv=None) -> dict:
                     help="engine of the FP32 products (bse_set_fp32_gemm: 0 SIMT, 1 in-kernel split, 2 pre-split)")
     ap.add_argument("--m", type=int, default=8192, help="matrix order (tridiag, tdeig)")
     ap.add_argument("--fp64", action="store_true", help="tridiag in FP64 instead of FP32")
+    ap.add_argument("--mrrr", action="store_true", help="tdeig by the representation tree (bse_stage_tdeig_mrrr)")
+    ap.add_argument("--gaptol", type=float, default=1e-3, help="tdeig --mrrr: relative gap of a singleton")
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
     L = bse.lib()
@@ -151,11 +153,18 @@ def run(argv=None) -> dict:
         e = torch.rand(m, dtype=torch.float64, device="cuda", generator=g) + 0.5
         lam = torch.empty(m // 2, dtype=torch.float64, device="cuda")
         Vs = torch.empty(m * (m // 2), dtype=torch.float64, device="cuda")
-        work = torch.empty(L.bse_stage_tdeig_worksize(m), dtype=torch.uint8, device="cuda")
-        fn = lambda: bse.check(L.bse_stage_tdeig(m, e.data_ptr(), lam.data_ptr(), Vs.data_ptr(), work.data_ptr(),
-                                                 st.data_ptr(), None), "tdeig")
+        if a.mrrr:
+            n = m // 2
+            work = torch.empty(L.bse_stage_tdeig_mrrr_worksize(m, n, m), dtype=torch.uint8, device="cuda")
+            fn = lambda: bse.check(L.bse_stage_tdeig_mrrr(m, None, e.data_ptr(), 1, n, m, a.gaptol, lam.data_ptr(),
+                                                          Vs.data_ptr(), n, 1, work.data_ptr(), st.data_ptr(), None),
+                                   "tdeig_mrrr")
+        else:
+            work = torch.empty(L.bse_stage_tdeig_worksize(m), dtype=torch.uint8, device="cuda")
+            fn = lambda: bse.check(L.bse_stage_tdeig(m, e.data_ptr(), lam.data_ptr(), Vs.data_ptr(), work.data_ptr(),
+                                                     st.data_ptr(), None), "tdeig")
         ms = _timed(torch, fn, a.reps)
-        out.update(m=m, ms=ms)
+        out.update(m=m, ms=ms, method="mrrr" if a.mrrr else "twisted")
     torch.cuda.synchronize()
     out["status"] = int(st[0].item())
     if out["status"] != 0:

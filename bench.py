@@ -360,12 +360,19 @@ def run_ours(args):
         lamh = torch.empty(n, dtype=torch.float64).pin_memory()
         Xh = torch.empty(m * n, dtype=torch.complex128).pin_memory()
         wh = torch.empty(n, dtype=torch.complex128).pin_memory()
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
+        def e2e_step():
             _, _, _, _, sol = ctx.solve(Ah, Bh, precision=args.precision, out={"lambda": lamh, "X": Xh}, keep=True)
             ctx.spectrum(sol, drh, dlh, out=wh)
             sol.free()
+
+        # untimed warm-up of the host-buffer path (the first kept solution grows the
+        # device memory pool, which then keeps it)
+        for _ in range(min(args.warmup, 2)):
+            e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
         barrier()
         te = (time.perf_counter() - t0) / args.e2e_steps
         e2e = {"value": ws / te, "unit": UNIT, "h2d_bytes_per_step": 2 * 16 * n * n + 2 * 16 * m,

@@ -39,6 +39,8 @@ namespace bse {
 
 static inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+constexpr int kRRMax = 32;      // largest cluster re-solved by Rayleigh-Ritz
+constexpr int kRRChunks = 8;    // row chunks of a cluster's Gram matrices and rotation (blocks per cluster)
 constexpr int kBandW = 48;      // band biorthogonalization: index distance 1..kBandW
 constexpr int kBandChunk = 16;  // couplings per thread block pass
 
@@ -51,6 +53,9 @@ struct RefWork {
   unsigned long long* maxes;  // [0] max resid, [1] max dlam (as ordered bit patterns)
   int* cid;                   // cluster id per column
   int2* clus;                 // (first column, size) per cluster
+  int* coff;                  // per cluster: first of its k^2 (a, b) pairs in rrpart / rrcoef
+  double2* rrpart;            // [pair][kRRChunks][2]: partial U^H P and U^H K U over row chunks
+  double2* rrcoef;            // [pair]: the cluster's rotation Cc (row-major k x k)
   void* oz;                   // digit-split tensor-core product workspace (M U)
   void* oz2;                  // same for the projections and the update
   double* Gbig;               // 2n x 2n: [Ur Ui]^T [Rr Ri]
@@ -94,7 +99,8 @@ size_t refine_worksize(int n) {
   const size_t m = 2 * (size_t)n;
   size_t b = 2 * al256(16 * m * n) + 6 * al256(4 * m * n) + 8 * al256(4 * (size_t)n * n) + 2 * al256(8 * (size_t)n) +
              al256(64) + al256(64) + al256(4 * (size_t)n) + al256(8 * ((size_t)n / 2 + 2)) +
-             al256(16 * (size_t)n * kBandW);
+             al256(16 * (size_t)n * kBandW) + al256(4 * ((size_t)n / 2 + 2)) +
+             al256(16 * 2 * kRRChunks * (size_t)kRRMax * n) + al256(16 * (size_t)kRRMax * n);
   if (refine_uses_tc(n)) {
     b += al256(ozaki_worksize((int)m, 2 * n, (int)m, ozaki_digits((int)m)));
     b += al256(ozaki_worksize(2 * n, 2 * n, (int)m, corr_digits(m)));
@@ -128,6 +134,10 @@ static RefWork carve_ref(void* work, int n) {
   w.maxes = (unsigned long long*)take(64);
   w.cid = (int*)take(4 * (size_t)n);
   w.clus = (int2*)take(8 * ((size_t)n / 2 + 2));
+  w.coff = (int*)take(4 * ((size_t)n / 2 + 2));
+  // clusters hold <= kRRMax of the n columns each, so their k^2 pairs number <= kRRMax n
+  w.rrpart = (double2*)take(16 * 2 * kRRChunks * (size_t)kRRMax * n);
+  w.rrcoef = (double2*)take(16 * (size_t)kRRMax * n);
   w.Bband = (double2*)take(16 * (size_t)n * kBandW);
   w.oz = w.oz2 = nullptr;
   w.Gbig = nullptr;
@@ -335,7 +345,6 @@ __global__ void ref_apply(long count, double* __restrict__ Ur, double* __restric
 // with B_I = L L^H, C = L^{-1} A_I L^{-H} diagonalised by cyclic complex Jacobi,
 // and U_I <- U_I Cc, P_I <- P_I Cc (P is linear in U), Cc = L^{-H} Z, so that
 // Cc^H B_I Cc = I (the Theorem 3 normalisation) and the mu come out ascending.
-constexpr int kRRMax = 32;
 
 struct cplx {
   double x, y;
@@ -348,8 +357,73 @@ __device__ __forceinline__ cplx cconjmul(cplx a, cplx b) { return {a.x * b.x + a
 __device__ __forceinline__ cplx cconj(cplx a) { return {a.x, -a.y}; }
 __device__ __forceinline__ cplx cscale(cplx a, double s) { return {a.x * s, a.y * s}; }
 
-__global__ void __launch_bounds__(256) ref_cluster_rr(int n, const int2* __restrict__ clusters, double* Ur, double* Ui,
-                                                      double* Pr, double* Pi, double* lam_out) {
+// The pencil's small matrices over the cluster's columns, in row chunks (one
+// block per cluster and chunk, so a large cluster's FP64 work spreads over the
+// GPU): partial A = U_I^H P_I and B = U_I^H K U_I over rows [i0, i1) of the top
+// half and the matching rows of the bottom half. The chunk's k columns are staged
+// in shared memory kRRRows rows at a time (coalesced loads); thread t sums pairs
+// t, t + 256, ... (k^2 <= 1024).
+constexpr int kRRRows = 16;
+
+__global__ void __launch_bounds__(256) ref_rr_gram(int n, const int2* __restrict__ clusters,
+                                                   const int* __restrict__ coff, const double* __restrict__ Ur,
+                                                   const double* __restrict__ Ui, const double* __restrict__ Pr,
+                                                   const double* __restrict__ Pi, double2* __restrict__ part) {
+  __shared__ cplx ut_s[kRRMax][kRRRows], ub_s[kRRMax][kRRRows], pt_s[kRRMax][kRRRows], pb_s[kRRMax][kRRRows];
+  const int2 cl = clusters[blockIdx.x];
+  const int c0 = cl.x, k = cl.y;
+  const int tid = threadIdx.x;
+  const long m = 2L * n;
+  const int R = (n + gridDim.y - 1) / gridDim.y;
+  const int i0 = blockIdx.y * R, i1 = min(n, i0 + R);
+  cplx sa[4], sb[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sa[q] = sb[q] = cmk(0, 0);
+  for (int ib = i0; ib < i1; ib += kRRRows) {
+    for (int e = tid; e < k * kRRRows; e += blockDim.x) {
+      const int a = e / kRRRows, r = e % kRRRows, i = ib + r;
+      const long col = (long)(c0 + a) * m;
+      const bool ok = i < i1;
+      ut_s[a][r] = ok ? cmk(Ur[col + i], Ui[col + i]) : cmk(0, 0);
+      ub_s[a][r] = ok ? cmk(Ur[col + n + i], Ui[col + n + i]) : cmk(0, 0);
+      pt_s[a][r] = ok ? cmk(Pr[col + i], Pi[col + i]) : cmk(0, 0);
+      pb_s[a][r] = ok ? cmk(Pr[col + n + i], Pi[col + n + i]) : cmk(0, 0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int pr = tid + 256 * q;
+      if (pr < k * k) {
+        const int a = pr % k, b = pr / k;
+#pragma unroll 4
+        for (int r = 0; r < kRRRows; ++r) {
+          const cplx ut = ut_s[a][r], ub = ub_s[a][r], vt = ut_s[b][r], vb = ub_s[b][r];
+          sa[q] = cadd(sa[q], cconjmul(ut, pt_s[b][r]));
+          sa[q] = cadd(sa[q], cconjmul(ub, pb_s[b][r]));
+          // (K u)_top = -i u_bot = (Ui_bot, -Ur_bot); (K u)_bot = i u_top = (-Ui_top, Ur_top)
+          sb[q] = cadd(sb[q], cconjmul(ut, cmk(vb.y, -vb.x)));
+          sb[q] = cadd(sb[q], cconjmul(ub, cmk(-vt.y, vt.x)));
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int pr = tid + 256 * q;
+    if (pr < k * k) {
+      double2* o = part + ((long)(coff[blockIdx.x] + pr) * gridDim.y + blockIdx.y) * 2;
+      o[0] = make_double2(sa[q].x, sa[q].y);
+      o[1] = make_double2(sb[q].x, sb[q].y);
+    }
+  }
+}
+
+// One block per cluster: the pencil A c = mu B c solved exactly (below), the
+// eigenvalues written to lam_out and the rotation Cc to coef.
+__global__ void __launch_bounds__(256) ref_rr_solve(int n, int nchunks, const int2* __restrict__ clusters,
+                                                    const int* __restrict__ coff, const double2* __restrict__ part,
+                                                    double2* __restrict__ coef, double* lam_out) {
   __shared__ cplx A[kRRMax][kRRMax + 1];
   __shared__ cplx Bm[kRRMax][kRRMax + 1];
   __shared__ cplx Z[kRRMax][kRRMax + 1];
@@ -360,24 +434,14 @@ __global__ void __launch_bounds__(256) ref_cluster_rr(int n, const int2* __restr
   const int2 cl = clusters[blockIdx.x];
   const int c0 = cl.x, k = cl.y;
   const int tid = threadIdx.x;
-  const long m = 2L * n;
-  // 1. A = U^H P and B = U^H K U over the cluster's columns, FP64, thread per (a, b)
+  // 1. A = U^H P and B = U^H K U: the row chunks' partial sums, added in chunk order
   for (int pr = tid; pr < k * k; pr += blockDim.x) {
     const int a = pr % k, b = pr / k;
-    const double* ura = Ur + (long)(c0 + a) * m;
-    const double* uia = Ui + (long)(c0 + a) * m;
-    const double* urb = Ur + (long)(c0 + b) * m;
-    const double* uib = Ui + (long)(c0 + b) * m;
-    const double* prb = Pr + (long)(c0 + b) * m;
-    const double* pib = Pi + (long)(c0 + b) * m;
+    const double2* p = part + (long)(coff[blockIdx.x] + pr) * nchunks * 2;
     cplx sa = cmk(0, 0), sb = cmk(0, 0);
-    for (int i = 0; i < n; ++i) {
-      const cplx ut = cmk(ura[i], uia[i]), ub = cmk(ura[n + i], uia[n + i]);
-      sa = cadd(sa, cconjmul(ut, cmk(prb[i], pib[i])));
-      sa = cadd(sa, cconjmul(ub, cmk(prb[n + i], pib[n + i])));
-      // (K u)_top = -i u_bot = (Ui_bot, -Ur_bot); (K u)_bot = i u_top = (-Ui_top, Ur_top)
-      sb = cadd(sb, cconjmul(ut, cmk(uib[n + i], -urb[n + i])));
-      sb = cadd(sb, cconjmul(ub, cmk(-uib[i], urb[i])));
+    for (int ch = 0; ch < nchunks; ++ch) {
+      sa = cadd(sa, cmk(p[2 * ch].x, p[2 * ch].y));
+      sb = cadd(sb, cmk(p[2 * ch + 1].x, p[2 * ch + 1].y));
     }
     A[a][b] = sa;
     Bm[a][b] = sb;
@@ -527,23 +591,49 @@ __global__ void __launch_bounds__(256) ref_cluster_rr(int n, const int2* __restr
   }
   __syncthreads();
   if (tid < k) lam_out[c0 + tid] = mu[order[tid]];
-  // U_I <- U_I Cc, P_I <- P_I Cc, one row per thread
-  for (long i = tid; i < m; i += blockDim.x) {
-    cplx u[kRRMax], pp[kRRMax];
-    for (int a = 0; a < k; ++a) {
-      u[a] = cmk(Ur[i + (long)(c0 + a) * m], Ui[i + (long)(c0 + a) * m]);
-      pp[a] = cmk(Pr[i + (long)(c0 + a) * m], Pi[i + (long)(c0 + a) * m]);
-    }
-    for (int b = 0; b < k; ++b) {
-      cplx su = cmk(0, 0), sp = cmk(0, 0);
+  for (int pr = tid; pr < k * k; pr += blockDim.x) {
+    const int a = pr / k, b = pr % k;  // Cc[a][b], row-major
+    coef[coff[blockIdx.x] + pr] = make_double2(A[a][b].x, A[a][b].y);
+  }
+}
+
+// U_I <- U_I Cc and P_I <- P_I Cc over rows of one chunk (one block per cluster
+// and chunk): thread per row, the k new entries of the row summed in registers
+// before any is stored (the update is in place).
+__global__ void __launch_bounds__(256) ref_rr_apply(int n, const int2* __restrict__ clusters,
+                                                    const int* __restrict__ coff, const double2* __restrict__ coef,
+                                                    double* Ur, double* Ui, double* Pr, double* Pi) {
+  __shared__ cplx C[kRRMax * kRRMax];
+  const int2 cl = clusters[blockIdx.x];
+  const int c0 = cl.x, k = cl.y;
+  const long m = 2L * n;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const double2 v = coef[coff[blockIdx.x] + e];
+    C[e] = cmk(v.x, v.y);
+  }
+  __syncthreads();
+  const long R = (m + gridDim.y - 1) / gridDim.y;
+  const long i0 = blockIdx.y * R, i1 = min(m, i0 + R);
+  for (long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      double* Xr = pass == 0 ? Ur : Pr;
+      double* Xi = pass == 0 ? Ui : Pi;
+      cplx acc[kRRMax];
+#pragma unroll
+      for (int b = 0; b < kRRMax; ++b) acc[b] = cmk(0, 0);
       for (int a = 0; a < k; ++a) {
-        su = cadd(su, cmul(u[a], A[a][b]));
-        sp = cadd(sp, cmul(pp[a], A[a][b]));
+        const cplx x = cmk(Xr[i + (long)(c0 + a) * m], Xi[i + (long)(c0 + a) * m]);
+#pragma unroll
+        for (int b = 0; b < kRRMax; ++b)
+          if (b < k) acc[b] = cadd(acc[b], cmul(x, C[a * k + b]));
       }
-      Ur[i + (long)(c0 + b) * m] = su.x;
-      Ui[i + (long)(c0 + b) * m] = su.y;
-      Pr[i + (long)(c0 + b) * m] = sp.x;
-      Pi[i + (long)(c0 + b) * m] = sp.y;
+#pragma unroll
+      for (int b = 0; b < kRRMax; ++b)
+        if (b < k) {
+          Xr[i + (long)(c0 + b) * m] = acc[b].x;
+          Xi[i + (long)(c0 + b) * m] = acc[b].y;
+        }
     }
   }
 }
@@ -561,6 +651,30 @@ constexpr double kFinalTauCap = BSE_FINAL_TAU_CAP;
 
 // Runs of consecutive eigenvalues with relative gaps below tau, split to at most
 // kRRMax at their widest internal gap; cluster_id[j] = first index of j's run.
+// Rayleigh-Ritz on every cluster: partial Gram matrices over row chunks, the small
+// pencils, the rotation of U and P (three launches). coff: host scratch for the
+// clusters' pair offsets (kept by the caller until the stream has consumed it).
+static int cluster_rr(int n, const std::vector<int2>& clusters, std::vector<int>& coff, RefWork& w, double* lam,
+                      cudaStream_t s) {
+  const int nc = (int)clusters.size();
+  coff.resize(nc);
+  int acc = 0;
+  for (int c = 0; c < nc; ++c) {
+    coff[c] = acc;
+    acc += clusters[c].y * clusters[c].y;
+  }
+  BSE_CUDA(cudaMemcpyAsync(w.clus, clusters.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
+  BSE_CUDA(cudaMemcpyAsync(w.coff, coff.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+  kcount(3);
+  ref_rr_gram<<<dim3(nc, kRRChunks), 256, 0, s>>>(n, w.clus, w.coff, w.Ur, w.Ui, w.Pr, w.Pi, w.rrpart);
+  BSE_LAUNCH_CHECK();
+  ref_rr_solve<<<nc, 256, 0, s>>>(n, kRRChunks, w.clus, w.coff, w.rrpart, w.rrcoef, lam);
+  BSE_LAUNCH_CHECK();
+  ref_rr_apply<<<dim3(nc, kRRChunks), 256, 0, s>>>(n, w.clus, w.coff, w.rrcoef, w.Ur, w.Ui, w.Pr, w.Pi);
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
 static void find_clusters(const std::vector<double>& lam, double tau, std::vector<int2>& out, std::vector<int>& id) {
   const int n = (int)lam.size();
   out.clear();
@@ -745,6 +859,7 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
   std::vector<double> hlam(n);
   std::vector<int2> clusters;
   std::vector<int> cid;
+  std::vector<int> coff;  // pair offsets of the clusters (cluster_rr)
   *dlam_first = 0;
   for (int it = 0;; ++it) {
     // P = M U, FP64-accurate: [Pr | Pi] = M [Ur | Ui]
@@ -790,10 +905,7 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
       find_clusters(hlam, fmin(kFinalTauCap, fmax(kFinalTauFloor, fmax(1e-13, 20.0 * dl_level))), clusters, cid);
       BSE_CUDA(cudaMemcpyAsync(w.cid, cid.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
       if (!clusters.empty()) {
-        BSE_CUDA(cudaMemcpyAsync(w.clus, clusters.data(), sizeof(int2) * clusters.size(), cudaMemcpyHostToDevice, s));
-        kcount(1);
-        ref_cluster_rr<<<(unsigned)clusters.size(), 256, 0, s>>>(n, w.clus, w.Ur, w.Ui, w.Pr, w.Pi, lam);
-        BSE_LAUNCH_CHECK();
+        BSE_TRY(cluster_rr(n, clusters, coff, w, lam, s));
       }
       BSE_CUDA(cudaMemsetAsync(w.maxes, 0, 16, s));
       kcount(1);
@@ -835,10 +947,8 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     find_clusters(hlam, tau, clusters, cid);
     BSE_CUDA(cudaMemcpyAsync(w.cid, cid.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
     if (!clusters.empty()) {
-      BSE_CUDA(cudaMemcpyAsync(w.clus, clusters.data(), sizeof(int2) * clusters.size(), cudaMemcpyHostToDevice, s));
-      kcount(2);
-      ref_cluster_rr<<<(unsigned)clusters.size(), 256, 0, s>>>(n, w.clus, w.Ur, w.Ui, w.Pr, w.Pi, lam);
-      BSE_LAUNCH_CHECK();
+      BSE_TRY(cluster_rr(n, clusters, coff, w, lam, s));
+      kcount(1);
       // statistics and FP32 copies again for the rotated columns
       BSE_CUDA(cudaMemsetAsync(w.maxes, 0, 16, s));
       ref_colstats<<<n, 256, 0, s>>>(n, w.Ur, w.Ui, w.Pr, w.Pi, w.Urf, w.Uif, w.Rrf, w.Rif, lam, w.lam_new, w.bnorm,
@@ -848,7 +958,16 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     }
     // the host vectors must outlive the asynchronous uploads above
     BSE_CUDA(cudaStreamSynchronize(s));
-    if (verbose) fprintf(stderr, "[bse refine] n=%d sweep %d: %zu clusters (tau %.1e)\n", n, it, clusters.size(), tau);
+    if (verbose) {
+      int kmax = 0, cols = 0, big = 0;
+      for (const int2& c : clusters) {
+        kmax = c.y > kmax ? c.y : kmax;
+        cols += c.y;
+        big += c.y >= 8;
+      }
+      fprintf(stderr, "[bse refine] n=%d sweep %d: %zu clusters (tau %.1e): %d columns, largest %d, %d of >= 8\n", n,
+              it, clusters.size(), tau, cols, kmax, big);
+    }
     if (refine_uses_tc(n) && !(tc32::mode() >= 1 && n % 2 == 0)) {
       // tensor cores: C1 = U^H R and C2 = U^T R from the one real 2n x 2n product
       // G = [Ur Ui]^T [Rr Ri]; each operand column (an eigenvector, a residual) has a

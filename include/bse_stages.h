@@ -234,16 +234,20 @@ int bse_tc_gemm_bf16(int M, int N, int K, const void* A, const void* B, int ldk,
 /* C (M x N FP64, column-major, ldc) = A B to FP64-level accuracy on the bf16
  * tensor cores by error-free digit splitting (Ozaki scheme): row i of A is the
  * K-vector A + i*lda (for a symmetric matrix stored column-major, the matrix
- * itself), column j of B is B + j*ldb. s digits of beta bits per operand
- * (beta = bse_ozaki_digit_bits(K): 7 for 256 <= K <= 32768) give about beta*s
- * bits relative to the largest entry of each row of A times that of each column
- * of B; 1 <= s <= 11, s (s+1)/2 tensor-core passes (digit pairs p + q < s). The
+ * itself), column j of B is B + j*ldb. s digits of beta bits per operand give
+ * about beta*s - 1 bits relative to the largest entry of each row of A times that
+ * of each column of B; beta is the largest width <= 8 for which the 256-deep chunk
+ * sums stay exact (K >= 256: beta <= 8) and one anti-diagonal's integer sum over
+ * K stays below 2^31 (K 2^(2 beta - 2) s < 2^31: beta = 8 for K = 16384 up to
+ * s = 7, 7 beyond); 1 <= s <= 11, s (s+1)/2 tensor-core passes (digit pairs
+ * p + q < s). The
  * tensor cores sum each pair exactly over 256-deep chunks and the chunks are
  * added as integers, so the result does not depend on the launch shape.
  * work: bse_ozaki_worksize bytes. */
 size_t bse_ozaki_worksize(int M, int N, int K, int s);
 /* Digit width beta (bits) the digit-split product uses for reduction length K
- * (K >= 1; BSE_ERR_ARG otherwise). */
+ * with one digit (K >= 1; BSE_ERR_ARG otherwise); more digits can lower it, see
+ * bse_ozaki_gemm. */
 int bse_ozaki_digit_bits(int K);
 int bse_ozaki_gemm(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C, int ldc, int s,
                    void* work, int* dev_status, void* stream);

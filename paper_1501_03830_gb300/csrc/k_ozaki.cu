@@ -4,19 +4,20 @@
 //   C = A B,   A_ik = sigma_i sum_p a^(p)_ik 2^{-beta (p+1)},
 //              B_kj = tau_j   sum_q b^(q)_kj 2^{-beta (q+1)}
 //
-// sigma_i, tau_j are powers of two bounding row i of A and column j of B, and
-// the digits a^(p), b^(q) are integers with |digit| <= 2^beta, exactly
-// representable in bf16. The tensor cores accumulate a digit pair's products
-// in FP32 over chunks of Kc = 256 (kTcChunkK) reduction steps; beta is chosen so
-// that Kc * 2^(2 beta) <= 2^22: every chunk sum is then an integer the FP32
-// accumulation holds exactly whatever its summation order, and the epilogue
-// adds the chunk sums in 32-bit integers (which bounds the whole-K sum of one
-// anti-diagonal of pairs below 2^31, a second condition on beta). Each digit
-// pair (p, q) with p + q < s is one tensor-core pass; the pairs of one
-// anti-diagonal p + q = d share their scale and their integer sum, and the
-// epilogue adds sigma_i tau_j 2^{-beta (d+2)} x (exact integer) to C in FP64.
-// With s digits per operand the result carries about beta*s bits relative to
-// sigma_i tau_j.
+// sigma_i, tau_j are powers of two (one above the magnitude of row i of A and
+// column j of B), and the digits a^(p), b^(q) are integers with
+// |digit| <= 2^(beta-1), exactly representable in bf16. The tensor cores
+// accumulate a digit pair's products in FP32 over chunks of Kc = 256 (kTcChunkK)
+// reduction steps; beta is chosen so that Kc * 2^(2 beta - 2) <= 2^22: every
+// chunk sum is then an integer the FP32 accumulation holds exactly whatever its
+// summation order, and the epilogue adds the chunk sums in 32-bit integers (which
+// bounds the whole-K sum of one anti-diagonal of pairs below 2^31, a second
+// condition on beta). Each digit pair (p, q) with p + q < s is one tensor-core
+// pass; the pairs of one anti-diagonal p + q = d share their scale and their
+// integer sum, and the epilogue adds sigma_i tau_j 2^{-beta (d+2)} x (exact
+// integer) to C in FP64. With s digits per operand the result carries about
+// beta*s - 1 bits relative to the magnitudes of the row and column (beta = 8 for
+// K = 16384 up to 7 digits: 55 bits with 28 pairs).
 //
 // Layout: A is given K-major (row i of A is A[i * lda + k], k contiguous; for a
 // symmetric matrix stored column-major that is the matrix itself), B column-
@@ -46,26 +47,36 @@ static int ceil_log2(long x) {
   return l;
 }
 
+// Exactness conditions for beta with s digits per operand (every digit bounded by
+// 2^(beta-1), so every digit product by 2^(2 beta - 2)): a chunk of Kc products
+// sums to at most Kc 2^(2 beta - 2) <= 2^22 (exact in FP32 and convertible by the
+// 1.5 * 2^23 shift), and one anti-diagonal's integer sum over the whole K (at
+// most s pairs) stays below 2^31. bf16 holds every |digit| <= 2^8 exactly.
+static bool beta_ok(int ldk, int beta, int s) {
+  const int lkc = ceil_log2(ldk < kTcChunkK ? ldk : kTcChunkK);
+  if (2 * beta - 2 > 22 - lkc) return false;
+  return (double)ldk * ldexp(1.0, 2 * beta - 2) * (double)s < 2147483648.0;
+}
+
 static OzakiPlan plan(int M, int N, int K, int s) {
   OzakiPlan p;
   p.M = M; p.N = N; p.K = K;
   p.ldk = (K + 63) / 64 * 64;
-  // chunk sums exact in FP32 and convertible by the 1.5 * 2^23 shift:
-  // Kc * 2^(2 beta) <= 2^22; bf16 holds |digit| <= 2^8 exactly
-  const int lkc = ceil_log2(p.ldk < kTcChunkK ? p.ldk : kTcChunkK);
-  p.beta = (22 - lkc) / 2;
-  if (p.beta > 8) p.beta = 8;
-  // one anti-diagonal's integer sum over the whole K stays below 2^31:
-  // |sum| <= K 2^(2 beta) (1 + (d - 1) / 4) with d <= kMaxDigits - 1
-  while (p.beta > 1 && (double)p.ldk * ldexp(1.0, 2 * p.beta) * (1.0 + (kMaxDigits - 2) / 4.0) >= 2147483648.0)
-    --p.beta;
+  p.beta = 8;
+  while (p.beta > 1 && !beta_ok(p.ldk, p.beta, s)) --p.beta;
   p.s = s;
   return p;
 }
 
+// s digits of beta bits carry beta s - 1 bits (the leading digit is bounded by
+// 2^(beta-1) like the others, see ozaki_split): the fewest digits for `bits`
 int ozaki_digits(int K, int bits) {
-  const OzakiPlan p = plan(1, 1, K, 1);
-  return (bits + p.beta - 1) / p.beta;
+  const int ldk = (K + 63) / 64 * 64;
+  for (int beta = 8; beta >= 1; --beta) {
+    const int s = (bits + 1 + beta - 1) / beta;
+    if (beta_ok(ldk, beta, s)) return s;
+  }
+  return bits + 1;
 }
 
 // digits of A and B, their scales, and one int32 M x N plane per anti-diagonal
@@ -76,11 +87,14 @@ size_t ozaki_worksize(int M, int N, int K, int s) {
 }
 
 // Digits on the integer pipe (FP64 arithmetic is slow on this GPU): x / 2^e is
-// first written as a 62-bit fixed-point integer X (|X| < 2^62; bits below
-// 2^-62 of the vector scale are dropped, far below the s*beta <= 56 bits
-// kept), then digit p is X rounded at bit 62 - beta (p+1) and subtracted:
-// X = sum_p d_p 2^(62 - beta (p+1)) + remainder, |d_0| <= 2^beta,
-// |d_p| <= 2^(beta-1) for p > 0, exactly the balanced digits of the scheme.
+// first written as a 62-bit fixed-point integer X (bits below 2^-62 of the vector
+// scale are dropped, far below the s*beta - 1 <= 63 bits kept), then digit p is X
+// rounded at bit 62 - beta (p+1) and subtracted:
+// X = sum_p d_p 2^(62 - beta (p+1)) + remainder, the balanced digits of the
+// scheme with |d_p| <= 2^(beta-1) for p > 0. The scale 2^e is one power of two
+// above the vector's magnitude (|x| / 2^e < 1/2, so |X| < 2^61), which bounds the
+// leading digit by 2^(beta-1) too: every digit product is then <= 2^(2 beta - 2),
+// and beta = 8 keeps the 256-long chunk sums within 2^22.
 __device__ __forceinline__ long long fixed62(double x, int e) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((b >> 52) & 0x7ff);
@@ -137,7 +151,7 @@ __global__ void __launch_bounds__(256) ozaki_split(const TI* __restrict__ X, lon
   __syncthreads();
   mx = 0;
   for (int w = 0; w < 8; ++w) mx = red[w] > mx ? red[w] : mx;
-  const int e = scale_exp(mx);
+  const int e = scale_exp(mx) + 1;  // |x| / 2^e < 1/2
   if (threadIdx.x == 0) scale[v] = ldexp(1.0, e);
   __nv_bfloat16* dv = D + v * (long)ldk;
   for (int k = threadIdx.x; k < ldk; k += 256) {
@@ -171,7 +185,7 @@ __global__ void __launch_bounds__(256) ozaki_split_rows(const TI* __restrict__ X
   if (ty == 0) {
     unsigned long long m2 = 0;
     for (int w = 0; w < 8; ++w) m2 = vmax[w][tx] > m2 ? vmax[w][tx] : m2;
-    const int e = scale_exp(m2);
+    const int e = scale_exp(m2) + 1;  // |x| / 2^e < 1/2
     vexp[tx] = m2 ? e : 1000000;  // 1e6 marks an all-zero vector
     if (v0 + tx < V) scale[v0 + tx] = ldexp(1.0, m2 ? e : 0);
   }
@@ -305,8 +319,9 @@ extern "C" size_t bse_ozaki_worksize(int M, int N, int K, int s) { return bse::o
 extern "C" int bse_ozaki_digit_bits(int K) { return K < 1 ? BSE_ERR_ARG : bse::plan(1, 1, K, 1).beta; }
 
 // C (M x N FP64, column-major, ldc) = A B with A K-major (row i at A + i*lda),
-// B column-major (column j at B + j*ldb), to about beta*s bits beyond the
-// row/column scales (beta = bse_ozaki_digit_bits(K)), on the tensor cores.
+// B column-major (column j at B + j*ldb), to about beta*s - 1 bits beyond the
+// row/column magnitudes (beta = bse_ozaki_digit_bits(K) for s up to the bound
+// that keeps one anti-diagonal's integer sum below 2^31), on the tensor cores.
 // work: bse_ozaki_worksize(M, N, K, s) bytes.
 extern "C" int bse_ozaki_gemm(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
                               int ldc, int s, void* work, int* dev_status, void* stream) {

@@ -62,23 +62,26 @@ struct RefWork {
   double2* Bband;             // n x kBandW couplings of the band biorthogonalization
 };
 
-// Bits carried by the FP64-accurate product M U (7-bit digits). The first sweep
-// starts from an FP32-level solution: 40 bits (6 digits). The second sweep's
-// residual sets the couplings y_i^H x_j of the final basis, which come out as
-// (product error) / gap: 50 bits (8 digits) -- measured at n = 8192, 46 bits there
-// raise the couplings of far pairs 50-100x (Table 1's biorthogonality 1e-12 ->
-// 1e-10). The product of a third pass is normally the final check, which only
-// feeds the reported residual, the Rayleigh quotients (eigenvalues within 2.4e-13
-// of the FP64 path at 46 bits) and the rotations inside clusters: 46 bits
-// (7 digits).
+// Bits carried by the FP64-accurate product M U (8-bit digits at m <= 16384, s
+// digits carrying 8 s - 1 bits; M keeps 7 digits, so at most 55 bits). The first
+// sweep starts from an FP32-level solution (scaled residual ~1e-8): 39 bits
+// (5 digits) put the product's error four orders below what that sweep corrects.
+// The second sweep's residual sets the couplings y_i^H x_j of the final basis,
+// which come out as (product error) / gap: 50 bits (7 digits, 55 bits) --
+// measured at n = 8192, 46 bits there raise the couplings of far pairs 50-100x
+// (Table 1's biorthogonality 1e-12 -> 1e-10). The product of a third pass is
+// normally the final check, which feeds the reported residual, the Rayleigh
+// quotients and the rotations inside clusters; those rotations set the couplings
+// of the closest pairs (relative gap 1.9e-6 at n = 8192), which 47 bits left at
+// 2e-10 against 1e-12 at 49: 48 bits (7 digits, 55 bits).
 #ifndef BSE_FIRST_SWEEP_BITS
-#define BSE_FIRST_SWEEP_BITS 40
+#define BSE_FIRST_SWEEP_BITS 39
 #endif
 #ifndef BSE_SECOND_SWEEP_BITS
 #define BSE_SECOND_SWEEP_BITS 50
 #endif
 #ifndef BSE_LATER_BITS
-#define BSE_LATER_BITS 46
+#define BSE_LATER_BITS 48
 #endif
 constexpr int kFirstSweepBits = BSE_FIRST_SWEEP_BITS;
 constexpr int kSecondSweepBits = BSE_SECOND_SWEEP_BITS;
@@ -866,10 +869,7 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
     if (refine_uses_tc(n)) {
       // M is symmetric, so its column-major storage is also its K-major row layout;
       // its digits are split once and reused by every sweep
-      // bits of the product per sweep: the first sweep starts from an FP32-level
-      // solution (scaled residual ~1e-8), where ~40 bits put the product's error
-      // three orders below what that sweep corrects; the second sweep carries 50
-      // bits and the third pass (normally the final check) 46
+      // bits of the product per sweep (see kFirstSweepBits): 39, then 50, then 48
       const int sd = ozaki_digits(m);
       const int bits = it == 0 ? kFirstSweepBits : (it == 1 ? kSecondSweepBits : kLaterBits);
       BSE_TRY(ozaki_gemm(m, 2 * n, m, M, m, w.Ur, m, w.Pr, m, sd, w.oz, it == 0, reinterpret_cast<int*>(st), s,

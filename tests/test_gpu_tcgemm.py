@@ -83,8 +83,12 @@ def test_ozaki_fp64_accuracy(M, N, K, s):
     ref = A @ B
     scale = np.abs(A) @ np.abs(B)
     beta = L.bse_ozaki_digit_bits(K)
-    assert beta == (7 if K >= 256 else beta)
-    bound = 8.0 * 2.0 ** (-beta * s) * np.max(np.abs(A)) * np.max(np.abs(B)) * K
+    assert beta == 8
+    # the anti-diagonal bound K 2^(2 beta - 2) s < 2^31 lowers beta for many digits
+    while K * 2.0 ** (2 * beta - 2) * s >= 2.0 ** 31:
+        beta -= 1
+    # s digits carry beta s - 1 bits relative to the row / column magnitudes
+    bound = 16.0 * 2.0 ** (-beta * s) * np.max(np.abs(A)) * np.max(np.abs(B)) * K
     assert np.max(np.abs(got - ref)) <= max(bound, 4e-16 * np.max(scale))
     # FP64-level: far below what FP32 accumulation gives
     assert np.max(np.abs(got - ref) / scale) <= 1e-12
@@ -92,8 +96,9 @@ def test_ozaki_fp64_accuracy(M, N, K, s):
 
 @pytest.mark.parametrize("M,N,K", [(384, 512, 4096), (512, 512, 1000), (256, 768, 16384)])
 def test_ozaki_exact_on_integer_inputs(M, N, K):
-    """Integer entries below 2^13 split into two 7-bit digits, so s = 3 digit
-    pairs (p + q < 3) cover every nonzero digit product; all sums are integers
+    """Integer entries below 2^13 need two 8-bit digits (the leading one held to
+    2^7), so s = 3 digit pairs (p + q < 3) cover every nonzero digit product; all
+    sums are integers
     below 2^53, so the result must equal the integer product exactly. Row
     magnitudes vary (rows scaled down by powers of two) so the per-row digit
     scales differ."""

@@ -22,7 +22,9 @@ size_t trd_worksize(int m);
 template <typename T>
 int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStream_t st, DevStatus* status);
 
-int tdeig(int m, const double* e, double* lam, double* Vs, double* work, DevStatus* st, cudaStream_t s);
+// vec_scratch (nullable): m x n doubles for the two-thread vector kernel
+int tdeig(int m, const double* e, double* lam, double* Vs, double* work, DevStatus* st, cudaStream_t s,
+          double* vec_scratch = nullptr);
 // the same eigenpairs (or any index range of a general symmetric tridiagonal) by the
 // MRRR representation tree (k_mrrr.cu); Z row-major m x ldz
 size_t tdeig_mrrr_worksize(int m, int nz);

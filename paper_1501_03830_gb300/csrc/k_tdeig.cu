@@ -276,6 +276,110 @@ __global__ void __launch_bounds__(32) tdeig_vectors(int m, int n, const double* 
   }
 }
 
+// The same vectors with two threads per eigenvalue (adjacent lanes): the forward
+// pivots D_k (into Vs) and the backward pivots R_k (into Rb, an m x n scratch with
+// Vs's layout) are independent chains, and so are the two recurrences outward
+// from the twist, so each thread runs one of each; the twist index (argmin
+// |gamma_k| over the two halves) and the norm are combined by a shuffle.
+__global__ void __launch_bounds__(64) tdeig_vectors2(int m, int n, const double* __restrict__ e,
+                                                     const double* __restrict__ scal, const double* __restrict__ lam,
+                                                     double* __restrict__ Vs, double* __restrict__ Rb) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = t >> 1, role = t & 1;
+  const bool live = j < n;
+  const long ld = n;
+  const double pivmin = scal[1];
+  const double l = live ? lam[j] : 0.0;
+  const double nl = -l;
+  double* z = Vs + (live ? j : 0);
+  double* r = Rb + (live ? j : 0);
+  if (live) {
+    if (role == 0) {
+      // forward: D_k = p_k / p_{k-1} (leading minors, p_{-1} = 1, p_0 = -l)
+      MinorPair f{1.0, nl};
+      if ((__double_as_longlong(f.p1) << 1) == 0) f.p1 = -0x1p-900;
+      z[0] = guard_pivot(f.p1 / f.p0, pivmin);
+      for (int k = 0; k < m - 1; ++k) {
+        const double a = e[k];
+        const double p2 = minor_next(nl, a * a, f);
+        f.p0 = f.p1;
+        f.p1 = p2;
+        z[(long)(k + 1) * ld] = guard_pivot(f.p1 / f.p0, pivmin);
+        if ((k & 7) == 7) minor_rescale(f);
+      }
+    } else {
+      // backward: R_k = q_k / q_{k+1} (trailing minors)
+      MinorPair b{1.0, nl};
+      if ((__double_as_longlong(b.p1) << 1) == 0) b.p1 = -0x1p-900;
+      r[(long)(m - 1) * ld] = guard_pivot(b.p1 / b.p0, pivmin);
+      for (int k = m - 2; k >= 0; --k) {
+        const double a = e[k];
+        const double q2 = minor_next(nl, a * a, b);
+        b.p0 = b.p1;
+        b.p1 = q2;
+        r[(long)k * ld] = guard_pivot(b.p1 / b.p0, pivmin);
+        if (((m - 2 - k) & 7) == 7) minor_rescale(b);
+      }
+    }
+  }
+  __syncwarp();
+  // twist: gamma_k = D_k + R_k + l, smallest |gamma_k| (ties: the larger k)
+  const int half = m / 2;
+  double gmin = 1.7976931348623157e308;
+  int tw = -1;
+  if (live) {
+    const int k0 = role == 0 ? 0 : half, k1 = role == 0 ? half : m;
+    for (int k = k1 - 1; k >= k0; --k) {
+      const double gk = fabs(z[(long)k * ld] + r[(long)k * ld] + l);
+      if (gk < gmin) {
+        gmin = gk;
+        tw = k;
+      }
+    }
+  }
+  const double g_o = __shfl_xor_sync(0xffffffffu, gmin, 1);
+  const int tw_o = __shfl_xor_sync(0xffffffffu, tw, 1);
+  // the upper half (role 1) wins ties, as a scan from the bottom would
+  if (role == 0 ? (g_o <= gmin) : (g_o < gmin)) tw = tw_o;
+  __syncwarp();
+  double nrm = 0.0;
+  if (live) {
+    if (role == 1) {
+      // upward from the twist: z_{k+1} = -(alpha_k / R_{k+1}) z_k (alpha_k = -e[k])
+      double zk = 1.0;
+      for (int k = tw; k < m - 1; ++k) {
+        const double c = e[k] / r[(long)(k + 1) * ld];
+        const double zn = c * zk;
+        z[(long)(k + 1) * ld] = zn;
+        nrm = fma(zn, zn, nrm);
+        zk = zn;
+      }
+    } else {
+      // downward: z_k = -(alpha_k / D_k) z_{k+1}
+      double zk = 1.0;
+      nrm = 1.0;
+      for (int k = tw - 1; k >= 0; --k) {
+        const double c = e[k] / z[(long)k * ld];
+        const double zn = c * zk;
+        z[(long)k * ld] = zn;
+        nrm = fma(zn, zn, nrm);
+        zk = zn;
+      }
+    }
+  }
+  __syncwarp();
+  nrm += __shfl_xor_sync(0xffffffffu, nrm, 1);
+  if (!live) return;
+  if (role == 0) z[(long)tw * ld] = 1.0;
+  const double inv = 1.0 / sqrt(nrm);
+  // each thread scales its part: role 0 rows <= tw, role 1 rows > tw
+  const int k0 = role == 0 ? 0 : tw + 1, k1 = role == 0 ? tw + 1 : m;
+  for (int k = k0; k < k1; ++k) {
+    const double sgn = (k & 2) ? -inv : inv;
+    z[(long)k * ld] *= sgn;
+  }
+}
+
 // ---- reorthogonalization (remark 2) ----------------------------------------------
 // Twisted-factorization vectors of close eigenvalues are orthogonal only to
 // O(eps ||T|| / gap): at n = 8192 the closest pairs (relative gaps ~1e-6)
@@ -387,7 +491,8 @@ int tdeig_reorth(int m, double* Vs, void* work, cudaStream_t s) {
   return BSE_OK;
 }
 
-int tdeig(int m, const double* e, double* lam, double* Vs, double* work, DevStatus* st, cudaStream_t s) {
+int tdeig(int m, const double* e, double* lam, double* Vs, double* work, DevStatus* st, cudaStream_t s,
+          double* vec_scratch) {
   const int n = m / 2;
   double* e2 = work;
   double* scal = work + m;
@@ -410,7 +515,10 @@ int tdeig(int m, const double* e, double* lam, double* Vs, double* work, DevStat
   BSE_LAUNCH_CHECK();
   if (Vs) {
     KprofScope ks(K_TDEIG_VEC, s, 7.0 * 8.0 * m * n, 0.0);
-    tdeig_vectors<<<ceil_div(n, 32), 32, 0, s>>>(m, n, e, scal, lam, Vs);
+    if (vec_scratch)
+      tdeig_vectors2<<<ceil_div(2L * n, 64), 64, 0, s>>>(m, n, e, scal, lam, Vs, vec_scratch);
+    else
+      tdeig_vectors<<<ceil_div(n, 32), 32, 0, s>>>(m, n, e, scal, lam, Vs);
   }
   BSE_LAUNCH_CHECK();
   return BSE_OK;
@@ -467,7 +575,8 @@ extern "C" int bse_stage_tdeig_noalloc(int m, const double* e, double* lam, doub
   // Every scratch value the kernels read is written earlier in the same call
   // (tdeig_prep fills alpha^2 and the scalars), so stale contents from a
   // previous call need no clearing.
-  return bse::tdeig(m, e, lam, Vs, work, reinterpret_cast<bse::DevStatus*>(dev_status), (cudaStream_t)stream);
+  return bse::tdeig(m, e, lam, Vs, work, reinterpret_cast<bse::DevStatus*>(dev_status), (cudaStream_t)stream,
+                    nullptr);
 }
 
 extern "C" size_t bse_stage_tdeig_reorth_worksize(int m) { return m >= 2 ? bse::tdeig_reorth_worksize(m) : 0; }
@@ -481,5 +590,5 @@ extern "C" int bse_stage_tdeig(int m, const double* e, double* lam, double* Vs, 
                                void* stream) {
   if (m < 2 || (m & 1) || !e || !lam || !work || !dev_status) return BSE_ERR_ARG;
   return bse::tdeig(m, e, lam, Vs, (double*)work, reinterpret_cast<bse::DevStatus*>(dev_status),
-                    (cudaStream_t)stream);
+                    (cudaStream_t)stream, nullptr);
 }

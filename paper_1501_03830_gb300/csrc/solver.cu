@@ -327,7 +327,8 @@ int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, co
       // cluster-safe vectors from the representation tree: no reorthogonalization
       BSE_TRY(tdeig_mrrr(m, nullptr, ws->e, 1, n, m, 1e-3, ws->lam, ws->Vs, n, 1, ws->scratch, ws->status, s));
     } else {
-      BSE_TRY(tdeig(m, ws->e, ws->lam, ws->Vs, (double*)ws->scratch, ws->status, s));
+      // X is free until the back-transform: the vector kernel's second pivot array
+      BSE_TRY(tdeig(m, ws->e, ws->lam, ws->Vs, (double*)ws->scratch, ws->status, s, ws->X));
       // the FP64 path has no refinement: its eigenvectors are reorthogonalized (remark 2)
       BSE_TRY(tdeig_reorth(m, ws->Vs, ws->scratch, s));
     }
@@ -355,8 +356,8 @@ int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, co
     if (tm) cudaEventRecord(ev[4], s);
     if (mrrr_fits(ws, m, n))
       BSE_TRY(tdeig_mrrr(m, nullptr, ws->e, 1, n, m, 1e-3, ws->lam, ws->Vs, n, 1, ws->scratch, ws->status, s));
-    else
-      BSE_TRY(tdeig(m, ws->e, ws->lam, ws->Vs, (double*)ws->scratch, ws->status, s));
+    else  // X is free until the back-transform: the vector kernel's second pivot array
+      BSE_TRY(tdeig(m, ws->e, ws->lam, ws->Vs, (double*)ws->scratch, ws->status, s, ws->X));
     if (tm) cudaEventRecord(ev[5], s);
     const bool refine_now = precision == BSE_MIXED_REFINED;
     BSE_TRY(backtransform<float>(m, ws->Lf, ws->ldw, W, ws->ldw, tau, ws->Vs, ws->lam, ws->X,

@@ -118,7 +118,7 @@ struct PanelArgs {
   T* dotpart2;
   double* e;
   T* tau;
-  unsigned* bar;  // [0] arrivals, [1] generation
+  unsigned* bar;  // [0] arrivals (monotonic within a launch)
   DevStatus* st;
   int vec;  // 16-byte vector loads of W are aligned (ldw multiple of 16 B / sizeof(T), W 16-B aligned)
   unsigned long long* trace;  // optional: [column][kTracePoints][trace_stride] globaltimer stamps
@@ -141,36 +141,36 @@ __device__ __forceinline__ void trace_point(const PanelArgs<T>& a, int col, int 
     a.trace[((long)col * kTracePoints + point) * a.trace_stride + blockIdx.x] = gtimer();
 }
 
-// Grid-wide barrier for a cooperative launch. The wait is bounded: after
-// `spin` polls (2^25, about 2 s, unless a test lowers it) it records
-// BSE_ERR_TIMEOUT and every block returns at its next barrier. A failure
-// recorded by any block (or an earlier stage) also makes all blocks return.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, DevStatus* st, long spin) {
+// Grid-wide barrier for a cooperative launch on a monotonic arrival counter
+// (bar[0], zeroed before every launch): the k-th barrier of the launch is passed
+// once the counter reaches k * gridDim.x, so the last block's arrival itself
+// releases the others (no reset, no second word). The arrival is a release atomic
+// (it publishes the block's writes, which __syncthreads ordered before it) and the
+// poll an acquire load. The wait is bounded: after `spin` polls (2^25, about 2 s,
+// unless a test lowers it) it records BSE_ERR_TIMEOUT and every block returns at
+// its next barrier. A failure recorded by any block (or an earlier stage) also
+// makes all blocks return.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, DevStatus* st, long spin) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
-    const unsigned g = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
+    ++epoch;
+    const unsigned target = epoch * gridDim.x;
+    unsigned v;
+    asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(v) : "l"(bar) : "memory");
+    ++v;
     int ok = 1;
-    if (arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long it = 0;
-      while (*vgen == g) {
-        if (++it > spin) {
-          set_status(st, BSE_ERR_TIMEOUT, 1);
-          ok = 0;
-          break;
-        }
-        // spin tightly first (the release usually comes within a few us), then back off
-        if (it > 256) __nanosleep(40);
+    long it = 0;
+    while ((int)(v - target) < 0) {
+      if (++it > spin) {
+        set_status(st, BSE_ERR_TIMEOUT, 1);
+        ok = 0;
+        break;
       }
+      // spin tightly first (the release usually comes within a few us), then back off
+      if (it > 256) __nanosleep(40);
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
     }
-    __threadfence();
     if (*(volatile int*)&st->code != 0) ok = 0;
     s_ok = ok;
   }
@@ -416,6 +416,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) trd_panel_kernel(
   T* VP = a.VP;
   T* PV = a.PV;
   const long ldvp = a.ldvp;
+  unsigned epoch = 0;  // barriers passed in this launch (thread 0)
   T* sdV = s_vec[0];
   T* sdP = s_vec[1];
   T* sVs = s_vec[2];
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) trd_panel_kernel(
     const int par = c & 1;
     trace_point(a, j, 0);
     // column j (updated by the previous column's phase D) is complete
-    if (!grid_barrier(a.bar, a.st, a.spin)) return;
+    if (!grid_barrier(a.bar, epoch, a.st, a.spin)) return;
     trace_point(a, j, 1);
 
     // ---------------- phase B/C ----------------
@@ -488,7 +489,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) trd_panel_kernel(
       a.dotpart2[(long)blockIdx.x * 2 * TRD_NB + d1slot] = t;
     }
     trace_point(a, j, 3);
-    if (!grid_barrier(a.bar, a.st, a.spin)) return;
+    if (!grid_barrier(a.bar, epoch, a.st, a.spin)) return;
     trace_point(a, j, 4);
 
     // ---------------- phase D (+ A of the next column) ----------------
@@ -946,7 +947,6 @@ int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStr
     return BSE_OK;
   }
   TrdWork<T> w = carve<T>(work, m);
-  BSE_CUDA(cudaMemsetAsync(w.bar, 0, 64, st));
   int dev = 0, nsm = 0, per_sm = 0;
   BSE_CUDA(cudaGetDevice(&dev));
   BSE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -991,6 +991,8 @@ int tridiagonalize(int m, T* W, long ldw, double* e, T* tau, void* work, cudaStr
         bytes += N * (N - 1.0) * 0.5 * sizeof(T);
         flops += 2.0 * N * (N - 1.0);
       }
+      // every launch counts its barriers from zero
+      BSE_CUDA(cudaMemsetAsync(w.bar, 0, 64, st));
       KprofScope ks(K_TRD_SYMV, st, bytes, flops);
       void* args[] = {&pa};
       BSE_CUDA(cudaLaunchCooperativeKernel((const void*)trd_panel_kernel<T>, dim3(grid), dim3(256), args, 0, st));

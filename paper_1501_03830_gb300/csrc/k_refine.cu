@@ -73,7 +73,9 @@ struct RefWork {
 // normally the final check, which feeds the reported residual, the Rayleigh
 // quotients and the rotations inside clusters; those rotations set the couplings
 // of the closest pairs (relative gap 1.9e-6 at n = 8192), which 47 bits left at
-// 2e-10 against 1e-12 at 49: 48 bits (7 digits, 55 bits).
+// 2e-10 against 1e-12 at 49: 48 bits (7 digits, 55 bits) when that product is
+// formed in full. It is normally formed as P + M dU instead (incremental_digits),
+// which carries at least kSecondSweepBits of U with far fewer digit pairs.
 #ifndef BSE_FIRST_SWEEP_BITS
 #define BSE_FIRST_SWEEP_BITS 39
 #endif
@@ -97,6 +99,22 @@ static int corr_digits(long m) { return ozaki_digits((int)m, 25); }
 #define BSE_REFINE_TC_MIN_M 256
 #endif
 static bool refine_uses_tc(int n) { return 2 * n >= BSE_REFINE_TC_MIN_M; }
+
+// Digits of dU for the incremental product P + M dU (third and later passes):
+// with r = max_j max_i |dU_ij| / max_i |U_ij|, s digits of dU (8 s - 1 bits of
+// dU's column scale) carry 8 s - 1 + log2(1/r) bits of U's, so
+// kSecondSweepBits relative to U (the accuracy asked of the second sweep's full
+// product) need s = digits(kSecondSweepBits - floor(log2(1/r))). Returns 0 for a
+// zero update and -1 (the full product) when dU is not small enough to save digits.
+static int incremental_digits(long m, double r) {
+  if (!(r >= 0.0)) return -1;
+  if (r == 0.0) return 0;
+  const int sd = ozaki_digits((int)m);
+  const int lg = (int)floor(-log2(r));
+  if (lg < 8) return -1;
+  const int s = ozaki_digits((int)m, std::max(1, kSecondSweepBits - lg));
+  return s < sd ? s : -1;
+}
 
 size_t refine_worksize(int n) {
   const size_t m = 2 * (size_t)n;
@@ -126,7 +144,7 @@ static RefWork carve_ref(void* work, int n) {
   w.Pr = (double*)take(16 * m * n); w.Pi = w.Pr + m * n;
   w.Urf = (float*)take(4 * m * n); w.Uif = (float*)take(4 * m * n);
   w.Rrf = (float*)take(8 * m * n); w.Rif = w.Rrf + m * n;  // [Rrf | Rif] contiguous
-  w.dUr = (float*)take(4 * m * n); w.dUi = (float*)take(4 * m * n);
+  w.dUr = (float*)take(8 * m * n); w.dUi = w.dUr + m * n;  // [dUr | dUi] contiguous
   w.G1 = (float*)take(4 * (size_t)n * n); w.G2 = (float*)take(4 * (size_t)n * n);
   w.G3 = (float*)take(4 * (size_t)n * n); w.G4 = (float*)take(4 * (size_t)n * n);
   w.Fa = (float*)take(4 * (size_t)n * n); w.Fb = (float*)take(4 * (size_t)n * n);
@@ -338,6 +356,39 @@ __global__ void ref_apply(long count, double* __restrict__ Ur, double* __restric
     Ur[i] += (double)dUr[i];
     Ui[i] += (double)dUi[i];
   }
+}
+
+__device__ __forceinline__ double block_max256(double v, double* red) {
+  for (int o = 16; o >= 1; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < 8; ++k) t = fmax(t, red[k]);
+  return t;
+}
+
+// U += dU one column per block, and the update's size relative to the vector,
+// max_i |dU_ij| / max_i |U_ij| (real and imaginary parts together), max over the
+// columns into *ratio (ordered bit pattern): it sets how many digits of dU the next
+// product M U = P + M dU needs (see incremental_digits).
+__global__ void __launch_bounds__(256) ref_apply_cols(int n, double* __restrict__ Ur, double* __restrict__ Ui,
+                                                      const float* __restrict__ dUr, const float* __restrict__ dUi,
+                                                      unsigned long long* __restrict__ ratio) {
+  __shared__ double red[8];
+  const long m = 2L * n, c = (long)blockIdx.x * m;
+  double du = 0.0, u = 0.0;
+  for (long i = c + threadIdx.x; i < c + m; i += 256) {
+    const double dr = (double)dUr[i], di = (double)dUi[i];
+    const double ur = Ur[i] + dr, ui = Ui[i] + di;
+    Ur[i] = ur;
+    Ui[i] = ui;
+    du = fmax(du, fmax(fabs(dr), fabs(di)));
+    u = fmax(u, fmax(fabs(ur), fabs(ui)));
+  }
+  du = block_max256(du, red);
+  u = block_max256(u, red);
+  if (threadIdx.x == 0 && du > 0.0) atomic_max_pos(ratio, u > 0.0 ? du / u : 1.0);
 }
 
 // ---- cluster Rayleigh-Ritz ---------------------------------------------------
@@ -863,10 +914,22 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
   std::vector<int2> clusters;
   std::vector<int> cid;
   std::vector<int> coff;  // pair offsets of the clusters (cluster_rr)
+  double upd_ratio = 1.0;  // max over the columns of max |dU| / max |U| of the last update
   *dlam_first = 0;
   for (int it = 0;; ++it) {
     // P = M U, FP64-accurate: [Pr | Pi] = M [Ur | Ui]
-    if (refine_uses_tc(n)) {
+    const int s_inc = it >= 2 ? incremental_digits(m, upd_ratio) : -1;
+    if (s_inc == 0) {
+      // the last update was zero: P = M U already
+    } else if (refine_uses_tc(n) && s_inc > 0) {
+      // P + M dU = M (U + dU) up to the FP64 rounding of U + dU (2^-53 of U): the
+      // third and later products add the last update's product to the rotated P
+      // of the sweep before (which kept P = M U), with dU's digits only as many as
+      // its size below U leaves to carry
+      OzOperand ma{M, m, false, false}, db{w.dUr, m, false, true};
+      BSE_TRY(ozaki_gemm_ex(ma, db, m, 2 * n, m, w.Pr, m, ozaki_digits(m), true, w.oz, false,
+                            reinterpret_cast<int*>(st), s, s_inc));
+    } else if (refine_uses_tc(n)) {
       // M is symmetric, so its column-major storage is also its K-major row layout;
       // its digits are split once and reused by every sweep
       // bits of the product per sweep (see kFirstSweepBits): 39, then 50, then 48
@@ -1002,8 +1065,18 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
       BSE_TRY(sweep_gemm(op, m, n, n, w.Uif, m, false, w.Fd, n, false, 1.0, w.dUi, m, s));
     }
     kcount(1);
-    ref_apply<<<1024, 256, 0, s>>>((long)m * n, w.Ur, w.Ui, w.dUr, w.dUi);
+    BSE_CUDA(cudaMemsetAsync(w.maxes + 2, 0, 8, s));
+    ref_apply_cols<<<n, 256, 0, s>>>(n, w.Ur, w.Ui, w.dUr, w.dUi, w.maxes + 2);
     BSE_LAUNCH_CHECK();
+    {
+      unsigned long long rb = 0;
+      BSE_CUDA(cudaMemcpyAsync(&rb, w.maxes + 2, 8, cudaMemcpyDeviceToHost, s));
+      BSE_CUDA(cudaStreamSynchronize(s));
+      memcpy(&upd_ratio, &rb, 8);
+    }
+    if (verbose)
+      fprintf(stderr, "[bse refine] n=%d sweep %d: update max |dU|/|U| %.3e (next product: %d digits of dU)\n", n, it,
+              upd_ratio, refine_uses_tc(n) && it + 1 >= 2 ? incremental_digits(m, upd_ratio) : -1);
     ++sweeps;
   }
   kcount(1);

@@ -378,6 +378,7 @@ __global__ void __launch_bounds__(256) ref_apply_cols(int n, double* __restrict_
   __shared__ double red[8];
   const long m = 2L * n, c = (long)blockIdx.x * m;
   double du = 0.0, u = 0.0;
+#pragma unroll 4
   for (long i = c + threadIdx.x; i < c + m; i += 256) {
     const double dr = (double)dUr[i], di = (double)dUi[i];
     const double ur = Ur[i] + dr, ui = Ui[i] + di;

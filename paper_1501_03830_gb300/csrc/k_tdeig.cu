@@ -505,12 +505,15 @@ int tdeig(int m, const double* e, double* lam, double* Vs, double* work, DevStat
     // lanes per eigenvalue: enough independent Sturm chains to cover the GPU,
     // few enough not to waste FP64 throughput on large problems
     KprofScope ks(K_TDEIG_BISECT, s, 0.0, 0.0);
+    // one warp per block (the kernel shares nothing across warps): the FP64 work
+    // then spreads over every SM instead of n L / 256 blocks (128 of 152 SMs at
+    // n = 8192)
     if (n >= 4096)
-      tdeig_msect<4><<<ceil_div((long)n * 4, 256), 256, 0, s>>>(m, n, e2, scal, lam, st);
+      tdeig_msect<4><<<ceil_div((long)n * 4, 32), 32, 0, s>>>(m, n, e2, scal, lam, st);
     else if (n >= 1024)
-      tdeig_msect<16><<<ceil_div((long)n * 16, 256), 256, 0, s>>>(m, n, e2, scal, lam, st);
+      tdeig_msect<16><<<ceil_div((long)n * 16, 32), 32, 0, s>>>(m, n, e2, scal, lam, st);
     else
-      tdeig_msect<32><<<ceil_div((long)n * 32, 256), 256, 0, s>>>(m, n, e2, scal, lam, st);
+      tdeig_msect<32><<<ceil_div((long)n * 32, 32), 32, 0, s>>>(m, n, e2, scal, lam, st);
   }
   BSE_LAUNCH_CHECK();
   if (Vs) {

@@ -14,11 +14,11 @@ It shares no code with the CUDA path. The modules:
   intermediate results of the device pipeline stage by stage.
 * :mod:`oracle.alg2` -- Algorithm 2 (real problems, Theorem 5): two Cholesky
   factorizations, the SVD of L2^T L1, and X1, X2 from it.
-* :mod:`oracle.sbr` -- the two-stage (band, then tridiagonal) reduction of W,
-  the groundwork for a two-stage device reduction (no kernel uses it yet).
+* :mod:`oracle.sbr` -- the two-stage (band, then tridiagonal) reduction of W:
+  the reference the device two-stage reduction is tested against.
 * :mod:`oracle.mrrr` -- tridiagonal eigenpairs by a representation tree
   (relatively robust L D L^T representations, child shifts for clusters,
-  twisted factorizations), the groundwork for cluster-safe device vectors.
+  twisted factorizations): the reference the device tree is tested against.
 
 :mod:`oracle.brute` adds a 50-digit mpmath eigen-decomposition of H for
 n <= 4, one of the pins that ties the oracle to something other than itself.

@@ -4,8 +4,8 @@ idea: Dhillon and Parlett, Linear Algebra Appl. 387, 2004), FP64 numpy.
 Test infrastructure only (see the package docstring). It restates, for the
 tridiagonal step of Algorithm 3 (Section 3.3, remark 2, which calls for
 reorthogonalization when high accuracy is wanted), the way to get orthogonal eigenvectors
-without reorthogonalization; no kernel uses it yet. Plain scalar loops, small
-sizes only.
+without reorthogonalization; the device tree is tested against it. Plain scalar
+loops (vectorized over shifts where the recurrence allows), small sizes only.
 
   root       T - sigma I = L D L^T with sigma below the spectrum (positive
              definite, hence a relatively robust representation)

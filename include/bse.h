@@ -15,6 +15,9 @@
  *   - Only the LOWER triangles of A and B are read (LAPACK 'L'); the upper
  *     triangles are implied by A = A^H and B = B^T and are never checked.
  *   - lambda is returned ascending; column j of X and Y belongs to lambda[j].
+ *   - Eigenvectors are unique up to a unit factor; the complex solves fix it so
+ *     that the largest-modulus entry of the top half of x_j (the first of equal
+ *     ones) is real and positive, y_j carrying the same factor.
  *   - Pointers may be host or device memory; the library tells them apart
  *     (cudaPointerGetAttributes). The caller owns every buffer it passes.
  *     The library owns its workspace and every bse_sol it hands out.

@@ -287,6 +287,78 @@ int negate_bottom(int n, double* Y, cudaStream_t s) {
   return BSE_OK;
 }
 
+// Phase convention of the returned eigenvectors (eigenvectors are unique up to a
+// unit factor; this fixes one for display and reproducibility): in each column
+// the largest-modulus entry of the top half of x_j (the first of equal ones) is
+// made real and positive. x_j and y_j are multiplied by the same unit factor,
+// which keeps y_j = diag(I, -I) x_j and Y^H X = I; the weights do not depend on it.
+__global__ void __launch_bounds__(256) canon_phase_kernel(int n, double2* __restrict__ X, double2* __restrict__ Y) {
+  __shared__ double sv[8];
+  __shared__ int si[8];
+  __shared__ double2 s_p;
+  __shared__ double s_h;
+  __shared__ int s_r;
+  const long m = 2L * n;
+  double2* x = X + (long)blockIdx.x * m;
+  double best = -1.0;
+  int bi = 0;
+  for (int i = threadIdx.x; i < n; i += 256) {  // increasing i: the first of equals stays
+    const double2 v = x[i];
+    const double a = v.x * v.x + v.y * v.y;
+    if (a > best) {
+      best = a;
+      bi = i;
+    }
+  }
+  for (int o = 16; o >= 1; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sv[threadIdx.x >> 5] = best;
+    si[threadIdx.x >> 5] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = sv[0];
+    int r = si[0];
+    for (int w = 1; w < 8; ++w)
+      if (sv[w] > b || (sv[w] == b && si[w] < r)) {
+        b = sv[w];
+        r = si[w];
+      }
+    const double2 v = x[r];
+    const double h = hypot(v.x, v.y);
+    s_p = h > 0.0 ? make_double2(v.x / h, -v.y / h) : make_double2(1.0, 0.0);  // conj(v) / |v|
+    s_h = h;
+    s_r = r;
+  }
+  __syncthreads();
+  const double2 p = s_p;
+  const double h = s_h;
+  const int r = s_r;
+  for (int i = threadIdx.x; i < m; i += 256) {
+    const double2 v = x[i];
+    x[i] = (i == r && h > 0.0) ? make_double2(h, 0.0) : make_double2(v.x * p.x - v.y * p.y, v.x * p.y + v.y * p.x);
+    if (Y) {
+      double2* y = Y + (long)blockIdx.x * m;
+      const double2 u = y[i];
+      y[i] = (i == r && h > 0.0) ? make_double2(h, 0.0) : make_double2(u.x * p.x - u.y * p.y, u.x * p.y + u.y * p.x);
+    }
+  }
+}
+
+static int canon_phase(int n, double* X, double* Y, cudaStream_t s) {
+  kcount(1);
+  canon_phase_kernel<<<n, 256, 0, s>>>(n, reinterpret_cast<double2*>(X), reinterpret_cast<double2*>(Y));
+  BSE_LAUNCH_CHECK();
+  return BSE_OK;
+}
+
 // Runs the whole pipeline on device-resident inputs into the workspace outputs
 // (ws->lam, ws->X, ws->Y). Stage events go to ev[0..8] when timing.
 // MRRR is selected and the workspace's scratch holds its tree (a workspace made
@@ -381,6 +453,8 @@ int run_pipeline(bse_ctx* c, Workspace* ws, int n, const double* dA, int lda, co
       }
     }
   }
+  // the real path makes its columns real by a phase of its own (real_vectors)
+  if (!real_blocks) BSE_TRY(canon_phase(n, ws->X, want_Y ? ws->Y : nullptr, s));
   if (tm) cudaEventRecord(ev[7], s);
   return BSE_OK;
 }

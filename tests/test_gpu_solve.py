@@ -136,3 +136,31 @@ def test_invalid_arguments():
     assert L.bse_solve(ctx.handle, 4, bse.ptr(A), 3, bse.ptr(A), 4, 0, bse.ptr(lam), None, None, None, None) == bse.BSE_ERR_ARG
     assert L.bse_solve(ctx.handle, 4, bse.ptr(A), 4, bse.ptr(A), 4, 7, bse.ptr(lam), None, None, None, None) == bse.BSE_ERR_ARG
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_refined"])
+@pytest.mark.parametrize("n", [3, 64, 300])
+def test_eigenvector_phase_convention(precision, n):
+    """The returned x_j have a fixed phase: the largest-modulus entry of the top
+    half (the first of equal ones) is real and positive, with y_j = diag(I, -I) x_j
+    exactly and the solution otherwise as before (residuals, projectors)."""
+    torch_cuda()
+    bse, ctx = _ctx()
+    p = make_problem(n, 3000 + n)
+    lam, X, Y, _, _ = ctx.solve(p.A, p.B, precision=precision, want_Y=True)
+    # an entry of (within rounding) the largest modulus of the top half is exactly
+    # real and positive in every column (which of two near-equal entries the kernel
+    # took is not re-derived here: a one-ulp tie could go either way)
+    top = X[:n]
+    mx = np.max(np.abs(top), axis=0)
+    lead = (top.imag == 0.0) & (top.real > 0.0) & (np.abs(top) >= mx * (1 - 1e-12))
+    assert np.all(lead.any(axis=0))
+    assert np.array_equal(Y[:n], X[:n]) and np.array_equal(Y[n:], -X[n:])
+    ref = D.solve(p.A, p.B)
+    tol = 1e-4 if precision == "mixed" else 1e-10
+    assert rel_err(lam, ref.lam) <= tol
+    if precision != "mixed":
+        assert np.max(D.scaled_residuals(p.A, p.B, lam, X)) <= 100 * n * EPS
+        if n <= 64:
+            assert projector_gap(X, ref.X, n) <= 1e-8
+    ctx.close()

@@ -934,6 +934,7 @@ int refine(int n, const double* M, double* lam, double* X, int max_sweeps, doubl
       // M is symmetric, so its column-major storage is also its K-major row layout;
       // its digits are split once and reused by every sweep
       // bits of the product per sweep (see kFirstSweepBits): 39, then 50, then 48
+      // (a later product is formed in full only when the update is too large for P + M dU)
       const int sd = ozaki_digits(m);
       const int bits = it == 0 ? kFirstSweepBits : (it == 1 ? kSecondSweepBits : kLaterBits);
       BSE_TRY(ozaki_gemm(m, 2 * n, m, M, m, w.Ur, m, w.Pr, m, sd, w.oz, it == 0, reinterpret_cast<int*>(st), s,
